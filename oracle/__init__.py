@@ -1,0 +1,257 @@
+"""FP64 CPU oracle for the Benchmark Streaming operations and CG.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / ``--impl reference`` leg are the only callers.
+The GPU library never imports, links or executes anything in this directory,
+and this directory imports nothing from the GPU package.
+
+``bs_oracle.c`` holds the definitions (Table 1 BS1-BS7, eq. scatter_def,
+eqs. global_system / assembled_stiff / assembled_mass, Algorithm 1); this
+module only compiles it with gcc and marshals numpy arrays through ctypes.
+
+Parity is pinned for every routine here by ``tests/test_oracle_pins.py``
+(closed forms, invariants, brute force and exact rational arithmetic).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libbs_oracle.so")
+_SOURCES = ["bs_oracle.c", "mlp_oracle.c"]
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc: -O2, no FP contraction, no fast-math."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
+_I = ctypes.POINTER(ctypes.c_int32)
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+_SIGS = {
+    "bso_copy": (None, [_i64, _D, _D]),
+    "bso_axpy": (None, [_i64, _dbl, _D, _dbl, _D]),
+    "bso_norm": (None, [_i64, _D, _D]),
+    "bso_dot": (_dbl, [_i64, _D, _D]),
+    "bso_cg_update": (_dbl, [_i64, _dbl, _D, _D, _D, _D]),
+    "bso_scatter": (None, [_i64, _I, _D, _D]),
+    "bso_gather": (None, [_i64, _i64, _I, _D, _D]),
+    "bso_valence": (None, [_i64, _i64, _I, _I]),
+    "bso_gll": (_int, [_int, _D, _D, _D]),
+    "bso_apply_A": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D]),
+    "bso_apply_local": (_int, [_int, _int, _dbl, _dbl, _D, _D, _D]),
+    "bso_diag_A": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D]),
+    "bso_cg": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int, _int,
+                      _D, _D, _D]),
+    "bso_pcg_jacobi": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int, _D]),
+    "bso_cg_ir_f32": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int,
+                             _dbl, _int, ctypes.POINTER(_int), _D]),
+}
+
+
+def lib():
+    """Build (if stale) and load the oracle shared library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _i(a):
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _ids(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------- BS1-BS5
+
+def copy(x):
+    """BS1 (Table 1): y = x."""
+    x = _f64(x)
+    y = np.empty_like(x)
+    lib().bso_copy(x.size, _d(x), _d(y))
+    return y
+
+
+def axpy(alpha, x, beta, y):
+    """BS2 (Table 1): returns fma(alpha, x, beta*y)."""
+    x = _f64(x)
+    y = _f64(y).copy()
+    lib().bso_axpy(x.size, float(alpha), _d(x), float(beta), _d(y))
+    return y
+
+
+def norm(x):
+    """BS3 (Table 1): returns (x.x, sqrt(x.x))."""
+    x = _f64(x)
+    out = np.zeros(2)
+    lib().bso_norm(x.size, _d(x), _d(out))
+    return float(out[0]), float(out[1])
+
+
+def dot(x, y):
+    """BS4 (Table 1): x.y."""
+    x, y = _f64(x), _f64(y)
+    return float(lib().bso_dot(x.size, _d(x), _d(y)))
+
+
+def cg_update(alpha, p, Ap, x, r):
+    """BS5 (Table 1, Algorithm 1 steps 8-10): returns (x', r', r'.r')."""
+    p, Ap = _f64(p), _f64(Ap)
+    x, r = _f64(x).copy(), _f64(r).copy()
+    rr = lib().bso_cg_update(x.size, float(alpha), _d(p), _d(Ap), _d(x), _d(r))
+    return x, r, float(rr)
+
+
+# ---------------------------------------------------------------- BS6/BS7
+
+def scatter(ids, qG, qL_init):
+    """BS7 (eq. scatter_def): q_L = Z q_G, masked entries keep qL_init."""
+    ids, qG = _ids(ids), _f64(qG)
+    qL = _f64(qL_init).copy()
+    lib().bso_scatter(ids.size, _i(ids), _d(qG), _d(qL))
+    return qL
+
+
+def gather(ids, qL, NG):
+    """BS6 (eq. scatter_def): q_G = Z^T q_L, ascending local order."""
+    ids, qL = _ids(ids), _f64(qL)
+    qG = np.empty(int(NG))
+    lib().bso_gather(ids.size, int(NG), _i(ids), _d(qL), _d(qG))
+    return qG
+
+
+def valence(ids, NG):
+    """diag(Z^T Z): the number of local copies of every global node."""
+    ids = _ids(ids)
+    v = np.empty(int(NG), dtype=np.int32)
+    lib().bso_valence(ids.size, int(NG), _i(ids), _i(v))
+    return v
+
+
+# ---------------------------------------------------------------- operator
+
+def gll(N):
+    """GLL nodes r, weights w and D[a, i] = l_i'(r_a) (Sec. 2, eq. basis)."""
+    r, w, D = np.zeros(N + 1), np.zeros(N + 1), np.zeros((N + 1) * (N + 1))
+    if lib().bso_gll(int(N), _d(r), _d(w), _d(D)):
+        raise ValueError(f"unsupported degree {N}")
+    return r, w, D.reshape(N + 1, N + 1)
+
+
+def _coef(coef):
+    return None if coef is None else _f64(coef)
+
+
+def apply_A(E, N, h, lam, ids, NG, p, coef=None):
+    """A p with A = Z^T (c S_L + lambda M_L) Z (eqs. global_system,
+    assembled_stiff, assembled_mass)."""
+    ids, p, coef = _ids(ids), _f64(p), _coef(coef)
+    Ap = np.empty(int(NG))
+    rc = lib().bso_apply_A(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG), _d(p), _d(Ap))
+    if rc:
+        raise RuntimeError(f"bso_apply_A failed ({rc})")
+    return Ap
+
+
+def apply_local(E, N, h, lam, uL, coef=None):
+    """Block-diagonal A_L u_L (no Z, no Z^T)."""
+    uL, coef = _f64(uL), _coef(coef)
+    out = np.empty_like(uL)
+    rc = lib().bso_apply_local(E, N, float(h), float(lam), _d(coef), _d(uL), _d(out))
+    if rc:
+        raise RuntimeError(f"bso_apply_local failed ({rc})")
+    return out
+
+
+def diag_A(E, N, h, lam, ids, NG, coef=None):
+    """diag(A) = Z^T diag(A_L)."""
+    ids, coef = _ids(ids), _coef(coef)
+    d = np.empty(int(NG))
+    rc = lib().bso_diag_A(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG), _d(d))
+    if rc:
+        raise RuntimeError(f"bso_diag_A failed ({rc})")
+    return d
+
+
+def cg(E, N, h, lam, ids, NG, b, x0=None, tol=1e-8, maxit=1000, fixed_iters=False, coef=None):
+    """Algorithm 1.  Returns (x, iters, alpha[], beta[], rr[])."""
+    ids, b, coef = _ids(ids), _f64(b), _coef(coef)
+    x = np.zeros(int(NG)) if x0 is None else _f64(x0).copy()
+    ha, hb, hr = np.zeros(maxit + 1), np.zeros(maxit + 1), np.zeros(maxit + 2)
+    it = lib().bso_cg(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG), _d(b), _d(x),
+                      float(tol), int(maxit), int(bool(fixed_iters)), _d(ha), _d(hb), _d(hr))
+    if it < 0:
+        raise RuntimeError(f"bso_cg failed ({it})")
+    return x, it, ha[:it], hb[:it], hr[:it + 1]
+
+
+def pcg_jacobi(E, N, h, lam, ids, NG, b, tol=1e-8, maxit=1000, coef=None):
+    """Jacobi-preconditioned CG.  Returns (x, iters, rr[])."""
+    ids, b, coef = _ids(ids), _f64(b), _coef(coef)
+    x = np.zeros(int(NG))
+    hr = np.zeros(maxit + 2)
+    it = lib().bso_pcg_jacobi(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG), _d(b),
+                              _d(x), float(tol), int(maxit), _d(hr))
+    if it < 0:
+        raise RuntimeError(f"bso_pcg_jacobi failed ({it})")
+    return x, it, hr[:it + 1]
+
+
+def cg_ir_f32(E, N, h, lam, ids, NG, b, outer_tol=1e-10, outer_maxit=50, inner_tol=1e-4,
+              inner_maxit=2000, coef=None):
+    """FP32-storage CG inside an FP64 iterative-refinement loop.
+    Returns (x, inner_iters, outer_iters, true_relres)."""
+    ids, b, coef = _ids(ids), _f64(b), _coef(coef)
+    x = np.zeros(int(NG))
+    outer = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    it = lib().bso_cg_ir_f32(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG), _d(b),
+                             _d(x), float(outer_tol), int(outer_maxit), float(inner_tol),
+                             int(inner_maxit), ctypes.byref(outer), ctypes.byref(rel))
+    if it < 0:
+        raise RuntimeError(f"bso_cg_ir_f32 failed ({it})")
+    return x, it, outer.value, rel.value

@@ -1,0 +1,539 @@
+/*
+ * bs_oracle.c -- plain, slow, FP64 CPU oracle for the Benchmark Streaming
+ * (BS1-BS7) operations and the conjugate-gradient iteration of
+ * Chalmers & Warburton, "Portable high-order finite element kernels I:
+ * Streaming Operations" (arXiv 2009.10917).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the benchmark's CPU-baseline leg may load this library.  The GPU library
+ * (libbs) never links, loads or calls it; the two share no source, header,
+ * table or helper.  Inputs reach both sides from a separate seeded generator.
+ *
+ * Every routine is the literal definition, in the paper's order and
+ * notation, so that it can be checked against the paper by eye: no blocking,
+ * no fusion, no reordering.  The file is compiled with -ffp-contract=off, so
+ * every fused multiply-add is an explicit fma() and every other product and
+ * sum is rounded on its own.
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *  - BS2 is y = fma(alpha, x, beta*y)                        (Table 1, BS2)
+ *  - BS3/BS4 return the correctly rounded sum as far as a doubled-precision
+ *    dot product (Ogita, Rump & Oishi 2005, "Dot2") gives it  (Table 1)
+ *  - BS6 sums the local copies of a global node in ascending local index,
+ *    starting from +0.0; a global node with no copies is 0  (eq. scatter_def)
+ *  - BS7 leaves masked (id < 0) local entries untouched      (Sec. 5)
+ *  - the operator is the affine-cube GLL spectral element discretisation of
+ *    the Helmholtz weak form with collocated (lumped) quadrature (Sec. 2)
+ *  - CG stops when r.r <= tol^2 * (b.b)                       (Algorithm 1)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Error-free transformations (Ogita, Rump & Oishi, SIAM J. Sci. Comput.    */
+/* 26(6), 2005): TwoSum (Knuth) and TwoProduct (by fma).                    */
+/* ------------------------------------------------------------------------ */
+static void two_sum(double a, double b, double *s, double *e) {
+  double x = a + b;
+  double z = x - a;
+  *s = x;
+  *e = (a - (x - z)) + (b - z);
+}
+
+static void two_prod(double a, double b, double *p, double *e) {
+  double x = a * b;
+  *p = x;
+  *e = fma(a, b, -x);
+}
+
+/* Dot2: sum of x_i*y_i as if accumulated in twice the working precision,
+ * then rounded once. */
+static double dot2(int64_t n, const double *x, const double *y) {
+  if (n <= 0) return 0.0;
+  double p, s, h, r, q;
+  two_prod(x[0], y[0], &p, &s);
+  for (int64_t i = 1; i < n; ++i) {
+    two_prod(x[i], y[i], &h, &r);
+    two_sum(p, h, &p, &q);
+    s = s + (q + r);
+  }
+  return p + s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BS1-BS5 (Table 1; Listings 1-3)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* BS1, vector copy: y = x. */
+void bso_copy(int64_t n, const double *x, double *y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = x[i];
+}
+
+/* BS2, vector AXPY: y = alpha*x + beta*y, read as fma(alpha, x, beta*y). */
+void bso_axpy(int64_t n, double alpha, const double *x, double beta, double *y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = fma(alpha, x[i], beta * y[i]);
+}
+
+/* BS3, vector norm: out[0] = x.x, out[1] = sqrt(x.x). */
+void bso_norm(int64_t n, const double *x, double *out) {
+  double s = dot2(n, x, x);
+  out[0] = s;
+  out[1] = sqrt(s);
+}
+
+/* BS4, inner product: x.y. */
+double bso_dot(int64_t n, const double *x, const double *y) {
+  return dot2(n, x, y);
+}
+
+/* BS5, fused CG update (Algorithm 1, steps 8-10 fused):
+ *   x = x + alpha p,  r = r - alpha Ap,  returns r.r of the updated r. */
+double bso_cg_update(int64_t n, double alpha, const double *p, const double *Ap,
+                     double *x, double *r) {
+  for (int64_t i = 0; i < n; ++i) {
+    x[i] = fma(alpha, p[i], x[i]);
+    r[i] = fma(-alpha, Ap[i], r[i]);
+  }
+  return dot2(n, r, r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* BS6/BS7: gather and scatter (eq. scatter_def; Listings 4-5)              */
+/* ------------------------------------------------------------------------ */
+
+/* BS7, scatter q_L = Z q_G: q_L[l] = q_G[ids[l]] where ids[l] >= 0; masked
+ * entries keep their previous value. */
+void bso_scatter(int64_t NL, const int32_t *ids, const double *qG, double *qL) {
+  for (int64_t l = 0; l < NL; ++l)
+    if (ids[l] >= 0) qL[l] = qG[ids[l]];
+}
+
+/* BS6, gather q_G = Z^T q_L: q_G[g] = sum of q_L[l] over {l : ids[l] = g},
+ * accumulated in ascending l from +0.0. */
+void bso_gather(int64_t NL, int64_t NG, const int32_t *ids, const double *qL,
+                double *qG) {
+  for (int64_t g = 0; g < NG; ++g) qG[g] = 0.0;
+  for (int64_t l = 0; l < NL; ++l)
+    if (ids[l] >= 0) qG[ids[l]] = qG[ids[l]] + qL[l];
+}
+
+/* Valence of every global node: the diagonal of Z^T Z. */
+void bso_valence(int64_t NL, int64_t NG, const int32_t *ids, int32_t *val) {
+  for (int64_t g = 0; g < NG; ++g) val[g] = 0;
+  for (int64_t l = 0; l < NL; ++l)
+    if (ids[l] >= 0) val[ids[l]] += 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Lobatto-Legendre nodes, weights and differentiation matrix         */
+/* (Sec. 2, eq. basis): the nodes are -1, +1 and the roots of P_N'.         */
+/* ------------------------------------------------------------------------ */
+
+/* Legendre P_N(x), P_N'(x) by the three-term recurrence
+ *   (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1},
+ * and P'_{k+1} = P'_{k-1} + (2k+1) P_k. */
+static void legendre(int N, double x, double *PN, double *dPN) {
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (N == 0) { *PN = 1.0; *dPN = 0.0; return; }
+  for (int k = 1; k < N; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    double d2 = d0 + (2.0 * k + 1.0) * p1;
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  *PN = p1;
+  *dPN = d1;
+}
+
+/* r[0..N], w[0..N], D[(N+1)*(N+1)] row-major: D[a*(N+1)+i] = l_i'(r_a).
+ * Returns 0 on success. */
+int bso_gll(int N, double *r, double *w, double *D) {
+  if (N < 1 || N > 32) return 1;
+  const double pi = 3.14159265358979323846;
+  r[0] = -1.0;
+  r[N] = 1.0;
+  /* interior nodes: Newton on P_N'(x) = 0 from Chebyshev-Lobatto guesses;
+   * P_N'' from the Legendre equation (1-x^2) P'' = 2x P' - N(N+1) P. */
+  for (int i = 1; i < N; ++i) {
+    double x = -cos(pi * i / N);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(N, x, &P, &dP);
+      double d2P = (2.0 * x * dP - N * (N + 1.0) * P) / (1.0 - x * x);
+      double dx = dP / d2P;
+      x -= dx;
+      if (fabs(dx) <= 1e-17) break;
+    }
+    r[i] = x;
+  }
+  /* enforce the symmetry r_i = -r_{N-i} */
+  for (int i = 0; i <= N / 2; ++i) {
+    double s = 0.5 * (r[N - i] - r[i]);
+    r[i] = -s;
+    r[N - i] = s;
+  }
+  if (N % 2 == 0) r[N / 2] = 0.0;
+  double PN[33];
+  for (int i = 0; i <= N; ++i) {
+    double dP;
+    legendre(N, r[i], &PN[i], &dP);
+    w[i] = 2.0 / (N * (N + 1.0) * PN[i] * PN[i]);
+  }
+  int Nq = N + 1;
+  for (int a = 0; a <= N; ++a)
+    for (int i = 0; i <= N; ++i) {
+      double v;
+      if (a != i)
+        v = PN[a] / (PN[i] * (r[a] - r[i]));
+      else if (a == 0)
+        v = -N * (N + 1.0) / 4.0;
+      else if (a == N)
+        v = N * (N + 1.0) / 4.0;
+      else
+        v = 0.0;
+      D[a * Nq + i] = v;
+    }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Operator A = Z^T (S_L + lambda M_L) Z  (eqs. global_system,              */
+/* assembled_stiff, assembled_mass).  Elements are affine cubes of side h;  */
+/* element e carries a stiffness coefficient c_e (1 when coef is NULL).     */
+/* Local node (i,j,k) of element e sits at l = e*Np + i + Nq*(j + Nq*k).    */
+/* On element e, with u the local values and quadrature on the GLL nodes:   */
+/*   (A_e u)_ijk = c_e (h/2) sum_q w_q grad l_ijk(q) . grad u(q)            */
+/*               + lambda (h/2)^3 w_i w_j w_k u_ijk                         */
+/* (reference gradient; the affine map contributes (2/h)^2 (h/2)^3 = h/2).  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int E, N;
+  double h, lambda;
+  const double *coef; /* per-element stiffness coefficient or NULL */
+  const int32_t *ids; /* local -> global, length E*(N+1)^3, < 0 masked */
+  int64_t NG;
+} bso_problem;
+
+static void element_apply(const bso_problem *P, const double *r, const double *w,
+                          const double *D, int e, const double *u, double *Au,
+                          double *ur, double *us, double *ut) {
+  (void)r;
+  const int N = P->N, Nq = N + 1;
+  const double ce = P->coef ? P->coef[e] : 1.0;
+  const double g = 0.5 * P->h;          /* (h/2): stiffness geometric factor */
+  const double m = g * g * g;           /* (h/2)^3: mass geometric factor     */
+#define IDX(i, j, k) ((i) + Nq * ((j) + Nq * (k)))
+  /* reference gradient of u at every quadrature node (a,b,c) */
+  for (int c = 0; c < Nq; ++c)
+    for (int b = 0; b < Nq; ++b)
+      for (int a = 0; a < Nq; ++a) {
+        double dr = 0.0, ds = 0.0, dt = 0.0;
+        for (int n = 0; n < Nq; ++n) {
+          dr = fma(D[a * Nq + n], u[IDX(n, b, c)], dr);
+          ds = fma(D[b * Nq + n], u[IDX(a, n, c)], ds);
+          dt = fma(D[c * Nq + n], u[IDX(a, b, n)], dt);
+        }
+        double wq = w[a] * w[b] * w[c];
+        ur[IDX(a, b, c)] = wq * dr;
+        us[IDX(a, b, c)] = wq * ds;
+        ut[IDX(a, b, c)] = wq * dt;
+      }
+  /* test with grad l_ijk: sum over quadrature nodes of D^T applied */
+  for (int k = 0; k < Nq; ++k)
+    for (int j = 0; j < Nq; ++j)
+      for (int i = 0; i < Nq; ++i) {
+        double s = 0.0;
+        for (int n = 0; n < Nq; ++n) {
+          s = fma(D[n * Nq + i], ur[IDX(n, j, k)], s);
+          s = fma(D[n * Nq + j], us[IDX(i, n, k)], s);
+          s = fma(D[n * Nq + k], ut[IDX(i, j, n)], s);
+        }
+        double mass = m * (w[i] * w[j] * w[k]) * u[IDX(i, j, k)];
+        Au[IDX(i, j, k)] = fma(ce * g, s, P->lambda * mass);
+      }
+#undef IDX
+}
+
+static int apply_A(const bso_problem *P, const double *p, double *Ap) {
+  const int N = P->N, Nq = N + 1, Np = Nq * Nq * Nq;
+  double r[33], w[33], D[33 * 33];
+  if (bso_gll(N, r, w, D)) return 1;
+  double *u = malloc(sizeof(double) * 5 * Np);
+  if (!u) return 2;
+  double *Au = u + Np, *ur = Au + Np, *us = ur + Np, *ut = us + Np;
+  for (int64_t gI = 0; gI < P->NG; ++gI) Ap[gI] = 0.0;
+  for (int e = 0; e < P->E; ++e) {
+    const int32_t *id = P->ids + (int64_t)e * Np;
+    for (int l = 0; l < Np; ++l) u[l] = id[l] >= 0 ? p[id[l]] : 0.0; /* Z p */
+    element_apply(P, r, w, D, e, u, Au, ur, us, ut);
+    for (int l = 0; l < Np; ++l) /* Z^T, ascending local index */
+      if (id[l] >= 0) Ap[id[l]] = Ap[id[l]] + Au[l];
+  }
+  free(u);
+  return 0;
+}
+
+int bso_apply_A(int E, int N, double h, double lambda, const double *coef,
+                const int32_t *ids, int64_t NG, const double *p, double *Ap) {
+  bso_problem P = {E, N, h, lambda, coef, ids, NG};
+  return apply_A(&P, p, Ap);
+}
+
+/* Element-local operator only (no Z, no Z^T): uL -> A_L uL. */
+int bso_apply_local(int E, int N, double h, double lambda, const double *coef,
+                    const double *uL, double *AuL) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  double r[33], w[33], D[33 * 33];
+  if (bso_gll(N, r, w, D)) return 1;
+  bso_problem P = {E, N, h, lambda, coef, NULL, 0};
+  double *tmp = malloc(sizeof(double) * 3 * Np);
+  if (!tmp) return 2;
+  for (int e = 0; e < E; ++e)
+    element_apply(&P, r, w, D, e, uL + (int64_t)e * Np, AuL + (int64_t)e * Np, tmp,
+                  tmp + Np, tmp + 2 * Np);
+  free(tmp);
+  return 0;
+}
+
+/* diag(A) = Z^T diag(A_L), with
+ *   diag(S_e)_ijk = (h/2) sum_q w_q |grad l_ijk(q)|^2
+ *                 = (h/2) (K_ii w_j w_k + w_i K_jj w_k + w_i w_j K_kk),
+ *   K_ii = sum_a w_a D_ai^2. */
+int bso_diag_A(int E, int N, double h, double lambda, const double *coef,
+               const int32_t *ids, int64_t NG, double *diag) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  double r[33], w[33], D[33 * 33], K[33];
+  if (bso_gll(N, r, w, D)) return 1;
+  for (int i = 0; i < Nq; ++i) {
+    double s = 0.0;
+    for (int a = 0; a < Nq; ++a) s = fma(w[a] * D[a * Nq + i], D[a * Nq + i], s);
+    K[i] = s;
+  }
+  const double g = 0.5 * h, m = g * g * g;
+  for (int64_t gI = 0; gI < NG; ++gI) diag[gI] = 0.0;
+  for (int e = 0; e < E; ++e) {
+    const double ce = coef ? coef[e] : 1.0;
+    for (int k = 0; k < Nq; ++k)
+      for (int j = 0; j < Nq; ++j)
+        for (int i = 0; i < Nq; ++i) {
+          int l = i + Nq * (j + Nq * k);
+          int32_t id = ids[(int64_t)e * Np + l];
+          if (id < 0) continue;
+          double s = K[i] * w[j] * w[k] + w[i] * K[j] * w[k] + w[i] * w[j] * K[k];
+          double v = ce * g * s + lambda * m * (w[i] * w[j] * w[k]);
+          diag[id] = diag[id] + v;
+        }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Conjugate gradients (Algorithm 1) on A u = b.                            */
+/* x holds the initial guess on entry and the solution on exit.             */
+/* Iterates until r.r <= tol^2 (b.b) or maxit; with fixed_iters != 0 runs   */
+/* exactly maxit iterations.  Optional histories (length >= maxit+1) record */
+/* alpha_j, beta_j and r_j.r_j (hist_rr[0] is r_0.r_0).                     */
+/* Returns the iteration count, or -1 on a breakdown (p.Ap <= 0 or not      */
+/* finite), -2 on an allocation failure.                                    */
+/* ------------------------------------------------------------------------ */
+int bso_cg(int E, int N, double h, double lambda, const double *coef,
+           const int32_t *ids, int64_t NG, const double *b, double *x, double tol,
+           int maxit, int fixed_iters, double *hist_alpha, double *hist_beta,
+           double *hist_rr) {
+  bso_problem P = {E, N, h, lambda, coef, ids, NG};
+  double *r = malloc(sizeof(double) * 3 * NG);
+  if (!r) return -2;
+  double *p = r + NG, *Ap = p + NG;
+  /* r_0 = b - A x */
+  if (apply_A(&P, x, Ap)) { free(r); return -2; }
+  for (int64_t i = 0; i < NG; ++i) r[i] = b[i] - Ap[i];
+  /* p = r */
+  for (int64_t i = 0; i < NG; ++i) p[i] = r[i];
+  double rr = dot2(NG, r, r);
+  const double eps = tol * tol * dot2(NG, b, b);
+  if (hist_rr) hist_rr[0] = rr;
+  int j = 0;
+  while (j < maxit && (fixed_iters || rr > eps)) {
+    apply_A(&P, p, Ap);
+    double pAp = dot2(NG, p, Ap);
+    if (!(pAp > 0.0) || !isfinite(pAp)) { free(r); return -1; }
+    double alpha = rr / pAp;                                  /* step 7  */
+    double rr_new = bso_cg_update(NG, alpha, p, Ap, x, r);    /* 8-10    */
+    double beta = rr_new / rr;                                /* step 10 */
+    for (int64_t i = 0; i < NG; ++i) p[i] = fma(1.0, r[i], beta * p[i]); /* 11 */
+    rr = rr_new;
+    if (hist_alpha) hist_alpha[j] = alpha;
+    if (hist_beta) hist_beta[j] = beta;
+    if (hist_rr) hist_rr[j + 1] = rr;
+    ++j;
+  }
+  free(r);
+  return j;
+}
+
+/* Jacobi-preconditioned CG: Algorithm 1 with z = diag(A)^{-1} r, alpha =
+ * r.z / p.Ap, beta = r_{j+1}.z_{j+1} / r_j.z_j, p = z + beta p.  Stops on the
+ * unpreconditioned r.r <= tol^2 (b.b). */
+int bso_pcg_jacobi(int E, int N, double h, double lambda, const double *coef,
+                   const int32_t *ids, int64_t NG, const double *b, double *x,
+                   double tol, int maxit, double *hist_rr) {
+  bso_problem P = {E, N, h, lambda, coef, ids, NG};
+  double *r = malloc(sizeof(double) * 5 * NG);
+  if (!r) return -2;
+  double *p = r + NG, *Ap = p + NG, *z = Ap + NG, *dg = z + NG;
+  bso_diag_A(E, N, h, lambda, coef, ids, NG, dg);
+  apply_A(&P, x, Ap);
+  for (int64_t i = 0; i < NG; ++i) r[i] = b[i] - Ap[i];
+  for (int64_t i = 0; i < NG; ++i) z[i] = r[i] / dg[i];
+  for (int64_t i = 0; i < NG; ++i) p[i] = z[i];
+  double rz = dot2(NG, r, z), rr = dot2(NG, r, r);
+  const double eps = tol * tol * dot2(NG, b, b);
+  if (hist_rr) hist_rr[0] = rr;
+  int j = 0;
+  while (j < maxit && rr > eps) {
+    apply_A(&P, p, Ap);
+    double pAp = dot2(NG, p, Ap);
+    if (!(pAp > 0.0) || !isfinite(pAp)) { free(r); return -1; }
+    double alpha = rz / pAp;
+    rr = bso_cg_update(NG, alpha, p, Ap, x, r);
+    for (int64_t i = 0; i < NG; ++i) z[i] = r[i] / dg[i];
+    double rz_new = dot2(NG, r, z);
+    double beta = rz_new / rz;
+    for (int64_t i = 0; i < NG; ++i) p[i] = fma(1.0, z[i], beta * p[i]);
+    rz = rz_new;
+    ++j;
+    if (hist_rr) hist_rr[j] = rr;
+  }
+  free(r);
+  return j;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32-storage CG inside an FP64 iterative-refinement loop.                */
+/* Outer (FP64): r = b - A x; stop when ||r|| <= outer_tol ||b||; solve     */
+/* A d = r approximately in FP32; x = x + d.                                */
+/* Inner (Algorithm 1 on A d = r): vectors and the operator in float;       */
+/* dot products of float vectors accumulated in double and the scalars     */
+/* alpha, beta formed in double, then rounded to float for the updates.     */
+/* Stops at d-residual <= inner_tol * ||r|| or inner_maxit.                 */
+/* Returns the total inner iteration count; *outer gets the outer count and */
+/* *relres the final FP64 true relative residual.                           */
+/* ------------------------------------------------------------------------ */
+static double dotf(int64_t n, const float *x, const float *y) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s = fma((double)x[i], (double)y[i], s);
+  return s;
+}
+
+static void element_apply_f32(int N, const float *w, const float *D, float g,
+                              float m, float ce, float lambda, const float *u,
+                              float *Au, float *ur, float *us, float *ut) {
+  const int Nq = N + 1;
+#define IDX(i, j, k) ((i) + Nq * ((j) + Nq * (k)))
+  for (int c = 0; c < Nq; ++c)
+    for (int b = 0; b < Nq; ++b)
+      for (int a = 0; a < Nq; ++a) {
+        float dr = 0.f, ds = 0.f, dt = 0.f;
+        for (int n = 0; n < Nq; ++n) {
+          dr = fmaf(D[a * Nq + n], u[IDX(n, b, c)], dr);
+          ds = fmaf(D[b * Nq + n], u[IDX(a, n, c)], ds);
+          dt = fmaf(D[c * Nq + n], u[IDX(a, b, n)], dt);
+        }
+        float wq = w[a] * w[b] * w[c];
+        ur[IDX(a, b, c)] = wq * dr;
+        us[IDX(a, b, c)] = wq * ds;
+        ut[IDX(a, b, c)] = wq * dt;
+      }
+  for (int k = 0; k < Nq; ++k)
+    for (int j = 0; j < Nq; ++j)
+      for (int i = 0; i < Nq; ++i) {
+        float s = 0.f;
+        for (int n = 0; n < Nq; ++n) {
+          s = fmaf(D[n * Nq + i], ur[IDX(n, j, k)], s);
+          s = fmaf(D[n * Nq + j], us[IDX(i, n, k)], s);
+          s = fmaf(D[n * Nq + k], ut[IDX(i, j, n)], s);
+        }
+        float mass = m * (w[i] * w[j] * w[k]) * u[IDX(i, j, k)];
+        Au[IDX(i, j, k)] = fmaf(ce * g, s, lambda * mass);
+      }
+#undef IDX
+}
+
+static void apply_A_f32(const bso_problem *P, const float *w, const float *D,
+                        const float *p, float *Ap, float *buf) {
+  const int N = P->N, Nq = N + 1, Np = Nq * Nq * Nq;
+  float *u = buf, *Au = u + Np, *ur = Au + Np, *us = ur + Np, *ut = us + Np;
+  const float g = (float)(0.5 * P->h), m = (float)(0.125 * P->h * P->h * P->h);
+  for (int64_t gI = 0; gI < P->NG; ++gI) Ap[gI] = 0.f;
+  for (int e = 0; e < P->E; ++e) {
+    const int32_t *id = P->ids + (int64_t)e * Np;
+    for (int l = 0; l < Np; ++l) u[l] = id[l] >= 0 ? p[id[l]] : 0.f;
+    element_apply_f32(N, w, D, g, m, P->coef ? (float)P->coef[e] : 1.f,
+                      (float)P->lambda, u, Au, ur, us, ut);
+    for (int l = 0; l < Np; ++l)
+      if (id[l] >= 0) Ap[id[l]] = Ap[id[l]] + Au[l];
+  }
+}
+
+int bso_cg_ir_f32(int E, int N, double h, double lambda, const double *coef,
+                  const int32_t *ids, int64_t NG, const double *b, double *x,
+                  double outer_tol, int outer_maxit, double inner_tol,
+                  int inner_maxit, int *outer, double *relres) {
+  bso_problem P = {E, N, h, lambda, coef, ids, NG};
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  double rq[33], wq[33], Dq[33 * 33];
+  float w[33], D[33 * 33];
+  if (bso_gll(N, rq, wq, Dq)) return -2;
+  for (int i = 0; i < Nq; ++i) w[i] = (float)wq[i];
+  for (int i = 0; i < Nq * Nq; ++i) D[i] = (float)Dq[i];
+  double *r = malloc(sizeof(double) * 2 * NG);
+  float *fb = malloc(sizeof(float) * (5 * NG + 5 * Np));
+  if (!r || !fb) { free(r); free(fb); return -2; }
+  double *Ax = r + NG;
+  float *d = fb, *rf = d + NG, *pf = rf + NG, *Apf = pf + NG, *rs = Apf + NG;
+  float *buf = rs + NG;
+  (void)rs;
+  const double bnorm = sqrt(dot2(NG, b, b));
+  int total = 0, k = 0;
+  double res = 0.0;
+  for (;;) {
+    apply_A(&P, x, Ax);
+    for (int64_t i = 0; i < NG; ++i) r[i] = b[i] - Ax[i];
+    res = sqrt(dot2(NG, r, r));
+    if (res <= outer_tol * bnorm || k >= outer_maxit) break;
+    /* inner FP32 CG on A d = r, d_0 = 0 */
+    for (int64_t i = 0; i < NG; ++i) {
+      d[i] = 0.f;
+      rf[i] = (float)r[i];
+      pf[i] = rf[i];
+    }
+    double rr = dotf(NG, rf, rf);
+    const double eps = inner_tol * inner_tol * rr;
+    int j = 0;
+    while (j < inner_maxit && rr > eps) {
+      apply_A_f32(&P, w, D, pf, Apf, buf);
+      double pAp = dotf(NG, pf, Apf);
+      if (!(pAp > 0.0) || !isfinite(pAp)) break;
+      float alpha = (float)(rr / pAp);
+      for (int64_t i = 0; i < NG; ++i) {
+        d[i] = fmaf(alpha, pf[i], d[i]);
+        rf[i] = fmaf(-alpha, Apf[i], rf[i]);
+      }
+      double rr_new = dotf(NG, rf, rf);
+      float beta = (float)(rr_new / rr);
+      for (int64_t i = 0; i < NG; ++i) pf[i] = fmaf(1.f, rf[i], beta * pf[i]);
+      rr = rr_new;
+      ++j;
+    }
+    total += j;
+    for (int64_t i = 0; i < NG; ++i) x[i] = x[i] + (double)d[i];
+    ++k;
+  }
+  if (outer) *outer = k;
+  if (relres) *relres = bnorm > 0.0 ? res / bnorm : res;
+  free(r);
+  free(fb);
+  return total;
+}

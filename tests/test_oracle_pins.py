@@ -1,0 +1,368 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Nothing here retypes the oracle's formulas: each check goes through an
+independent route -- exact rational arithmetic, closed forms from the GLL
+rule, numpy polynomial algebra, dense Kronecker-product assembly, brute-force
+loops, invariants of Z (eq. scatter_def) and of CG (Algorithm 1).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_10917_gb300 import synth
+from tests import fem_ref
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def exact_dot(x, y):
+    """Correctly rounded sum of x_i y_i via exact rationals."""
+    s = sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x, y)), Fraction(0))
+    return float(s)
+
+
+def split_dot(x, y):
+    """Correctly rounded dot: Veltkamp splits make every partial product
+    exact in double; math.fsum rounds the exact sum once."""
+    def split(a):
+        c = 134217729.0 * a  # 2^27 + 1
+        hi = c - (c - a)
+        return hi, a - hi
+    xh, xl = split(np.asarray(x, dtype=np.float64))
+    yh, yl = split(np.asarray(y, dtype=np.float64))
+    terms = np.concatenate([xh * yh, xh * yl, xl * yh, xl * yl])
+    return math.fsum(terms.tolist())
+
+
+def ulp_close(a, b, ulps=2):
+    return abs(a - b) <= ulps * np.spacing(max(abs(a), abs(b), 1e-300))
+
+
+# ------------------------------------------------------------------ GLL
+
+def _golden_gll():
+    env = {"sqrt": math.sqrt, "__builtins__": {}}
+    out = {}
+    with open(os.path.join(GOLDEN, "gll_closed_forms.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            tok = line.split()
+            N, kind = int(tok[1]), tok[2]
+            if kind == "D":
+                row = int(tok[3])
+                vals = [eval(t, env) for t in tok[4:]]
+                out.setdefault((N, "D"), {})[row] = vals
+            else:
+                out[(N, kind)] = [eval(t, env) for t in tok[3:]]
+    return out
+
+
+def test_gll_closed_forms():
+    g = _golden_gll()
+    for N in (1, 2, 3, 4):
+        r, w, D = oracle.gll(N)
+        np.testing.assert_allclose(r, g[(N, "r")], rtol=0, atol=2e-16)
+        np.testing.assert_allclose(w, g[(N, "w")], rtol=0, atol=4e-16)
+        if (N, "D") in g:
+            for a, row in g[(N, "D")].items():
+                np.testing.assert_allclose(D[a], row, rtol=0, atol=4e-16)
+
+
+@pytest.mark.parametrize("N", range(1, 16))
+def test_gll_vs_numpy(N):
+    r, w, D = oracle.gll(N)
+    rn, wn, Dn = fem_ref.gll_np(N)
+    np.testing.assert_allclose(r, rn, atol=1e-14)
+    np.testing.assert_allclose(w, wn, atol=1e-14)
+    np.testing.assert_allclose(D, Dn, atol=1e-11 * max(1, N * N))
+
+
+@pytest.mark.parametrize("N", range(1, 16))
+def test_gll_quadrature_and_differentiation_exact(N):
+    r, w, D = oracle.gll(N)
+    assert abs(w.sum() - 2.0) < 1e-14
+    for k in range(2 * N):  # exact through degree 2N-1
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(w, r ** k) - exact) < 1e-13
+    assert np.max(np.abs(D @ np.ones(N + 1))) < 1e-12 * N * N
+    for k in range(1, N + 1):  # D is exact on polynomials of degree <= N
+        np.testing.assert_allclose(D @ r ** k, k * r ** (k - 1), atol=1e-11 * N * N)
+
+
+# ------------------------------------------------------------------ BS1-BS5
+
+def test_copy_bitwise():
+    x = synth.uniform(10007, 3)
+    assert np.array_equal(oracle.copy(x).view(np.uint64), x.view(np.uint64))
+    assert oracle.copy(np.zeros(0)).size == 0
+
+
+@pytest.mark.parametrize("beta", [1.0, 0.0, -0.25, 0.7])
+def test_axpy_exact_rational(beta):
+    x, y = synth.uniform(3000, 1, 0), synth.uniform(3000, 1, 1)
+    alpha = 0.5 if beta == 1.0 else -1.3
+    got = oracle.axpy(alpha, x, beta, y)
+    for i in range(x.size):
+        by = float(beta * y[i])  # the product beta*y is rounded on its own
+        want = float(Fraction(alpha) * Fraction(float(x[i])) + Fraction(by))
+        assert got[i] == want, i
+
+
+def test_axpy_fma_visible():
+    # a case where fma(alpha, x, y) differs from the twice-rounded alpha*x + y
+    alpha, x, y = 1.0 + 2.0 ** -30, 1.0 + 2.0 ** -30, -(1.0 + 2.0 ** -29)
+    got = oracle.axpy(alpha, np.array([x]), 1.0, np.array([y]))[0]
+    assert got == 2.0 ** -60
+    assert alpha * x + y == 0.0
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 3001])
+def test_dot_and_norm_exact_rational(n):
+    x, y = synth.uniform(n, 5, 0), synth.uniform(n, 5, 1)
+    assert ulp_close(oracle.dot(x, y), exact_dot(x, y), 1)
+    s, nrm = oracle.norm(x)
+    assert ulp_close(s, exact_dot(x, x), 1)
+    assert s == oracle.dot(x, x)
+    assert nrm == math.sqrt(s)
+
+
+def test_dot_large_exact():
+    n = 1 << 20
+    x, y = synth.uniform(n, 9, 0), synth.uniform(n, 9, 1)
+    assert ulp_close(oracle.dot(x, y), split_dot(x, y), 1)
+
+
+def test_dot_ill_conditioned():
+    x = np.array([1e16, 1.0, -1e16, 3.0, 1e-3])
+    y = np.array([1.0, 1.0, 1.0, 1.0, 1.0])
+    # condition number ~5e15: Dot2 stays within one ulp of the exact 4.001,
+    # where plain left-to-right summation returns 3.001
+    assert exact_dot(x, y) == 4.001
+    assert ulp_close(oracle.dot(x, y), 4.001, 1)
+    naive = 0.0
+    for v in x:
+        naive += v
+    assert abs(naive - 4.001) > 0.5
+    assert oracle.dot(np.zeros(0), np.zeros(0)) == 0.0
+
+
+def test_cg_update_exact():
+    n = 2000
+    p, Ap, x, r = (synth.uniform(n, 11, s) for s in range(4))
+    alpha = 0.37
+    x2, r2, rr = oracle.cg_update(alpha, p, Ap, x, r)
+    for i in range(0, n, 7):
+        assert x2[i] == float(Fraction(alpha) * Fraction(float(p[i])) + Fraction(float(x[i])))
+        assert r2[i] == float(-Fraction(alpha) * Fraction(float(Ap[i])) + Fraction(float(r[i])))
+    assert ulp_close(rr, exact_dot(r2, r2), 1)
+
+
+# ------------------------------------------------------------------ BS6/BS7
+
+def _masked_ids(mesh, frac=0.1, seed=3):
+    ids = mesh.ids.copy()
+    u = synth.uniform(ids.size, seed, 0, 0.0, 1.0)
+    ids[u < frac] = -1
+    return ids
+
+
+@pytest.mark.parametrize("K,N", [(2, 1), (2, 3), (3, 2)])
+def test_scatter_bruteforce(K, N):
+    m = synth.Mesh(K, N, seed=4)
+    ids = _masked_ids(m)
+    qG = synth.uniform(m.NG, 2)
+    init = np.full(m.NL, -7.25)
+    got = oracle.scatter(ids, qG, init)
+    for l in range(m.NL):
+        want = qG[ids[l]] if ids[l] >= 0 else -7.25
+        assert got[l] == want
+
+
+@pytest.mark.parametrize("K,N", [(2, 1), (2, 3), (3, 2)])
+def test_gather_bruteforce_ascending(K, N):
+    m = synth.Mesh(K, N, seed=5)
+    ids = _masked_ids(m, 0.05, 9)
+    qL = synth.uniform(m.NL, 6)
+    got = oracle.gather(ids, qL, m.NG)
+    for g in range(m.NG):
+        s = 0.0
+        for l in np.nonzero(ids == g)[0]:  # ascending l
+            s = s + qL[l]
+        assert got[g] == s
+    Z = fem_ref.scatter_matrix(ids, m.NG)
+    np.testing.assert_allclose(got, Z.T @ qL, rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("K,N", [(1, 1), (2, 2), (3, 3), (4, 5)])
+def test_Z_invariants(K, N):
+    m = synth.Mesh(K, N, seed=2)
+    v = oracle.valence(m.ids, m.NG)
+    # gather(scatter(1)) = valence, sum of valences = N_L
+    ones = oracle.scatter(m.ids, np.ones(m.NG), np.zeros(m.NL))
+    assert np.array_equal(oracle.gather(m.ids, ones, m.NG), v.astype(np.float64))
+    assert int(v.sum()) == m.NL
+    # structured mesh: a node's valence is the product over axes of 2 on an
+    # interior element face plane, else 1
+    G = m.G
+    g = np.arange(m.NG)
+    axis = lambda t: np.where((t % N == 0) & (t > 0) & (t < G - 1), 2, 1)
+    assert np.array_equal(v, axis(g % G) * axis((g // G) % G) * axis(g // (G * G)))
+    if m.NL <= 4096:
+        Z = fem_ref.scatter_matrix(m.ids, m.NG)
+        ZtZ = Z.T @ Z
+        assert np.array_equal(ZtZ, np.diag(v.astype(np.float64)))
+
+
+# ------------------------------------------------------------------ operator
+
+@pytest.mark.parametrize("K,N", [(1, 1), (1, 2), (2, 1), (2, 2), (2, 3), (1, 4)])
+@pytest.mark.parametrize("use_coef", [False, True])
+def test_operator_vs_dense(K, N, use_coef):
+    m = synth.Mesh(K, N, seed=8)
+    coef = synth.lognormal(m.E, 3) if use_coef else None
+    lam = 0.7
+    A = fem_ref.assemble(m, lam, coef)
+    np.testing.assert_allclose(A, A.T, atol=1e-14 * np.abs(A).max())
+    assert np.linalg.eigvalsh(A).min() > 0
+    p = synth.uniform(m.NG, 4)
+    got = oracle.apply_A(m.E, N, m.h, lam, m.ids, m.NG, p, coef)
+    scale = np.abs(A) @ np.abs(p)
+    assert np.all(np.abs(got - A @ p) <= 1e-13 * scale)
+    d = oracle.diag_A(m.E, N, m.h, lam, m.ids, m.NG, coef)
+    np.testing.assert_allclose(d, np.diag(A), rtol=1e-14)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7])
+def test_operator_closed_forms(N):
+    K = 2 if N <= 3 else 1
+    m = synth.Mesh(K, N, seed=1)
+    x, y, z = fem_ref.global_coords(m)
+    S = lambda u: oracle.apply_A(m.E, N, m.h, 0.0, m.ids, m.NG, u)
+    Mv = lambda u: oracle.apply_A(m.E, N, m.h, 1.0, m.ids, m.NG, u, np.zeros(m.E))
+    one = np.ones(m.NG)
+    assert np.max(np.abs(S(one))) < 1e-13          # grad of a constant is 0
+    assert abs(one @ Mv(one) - 1.0) < 1e-14          # volume of the unit cube
+    assert abs(x @ S(x) - 1.0) < 1e-13               # int |grad x|^2 = 1
+    if N >= 2:                                       # GLL exact to degree 2N-1
+        xy = x * y
+        assert abs(xy @ S(xy) - 2.0 / 3.0) < 1e-13   # int y^2 + x^2 = 2/3
+        assert abs(x @ Mv(x) - 1.0 / 3.0) < 1e-14    # int x^2 = 1/3
+
+
+def test_apply_local_vs_dense():
+    N, E, h = 3, 3, 0.25
+    S, M = fem_ref.element_matrices(N, h)
+    coef = np.array([1.0, 2.5, 0.3])
+    uL = synth.uniform(E * (N + 1) ** 3, 7)
+    got = oracle.apply_local(E, N, h, 0.4, uL, coef)
+    Np = (N + 1) ** 3
+    for e in range(E):
+        A = coef[e] * S + 0.4 * M
+        u = uL[e * Np:(e + 1) * Np]
+        assert np.all(np.abs(got[e * Np:(e + 1) * Np] - A @ u) <= 1e-13 * (np.abs(A) @ np.abs(u)))
+
+
+# ------------------------------------------------------------------ CG
+
+@pytest.mark.parametrize("K,N", [(1, 1), (1, 2)])
+def test_cg_exact_in_n_steps(K, N):
+    m = synth.Mesh(K, N, seed=1)
+    A = fem_ref.assemble(m, 1.0)
+    b = synth.uniform(m.NG, 12)
+    x, it, *_ = oracle.cg(m.E, N, m.h, 1.0, m.ids, m.NG, b, tol=1e-12, maxit=m.NG)
+    assert it <= m.NG
+    assert np.linalg.norm(b - A @ x) <= 1e-12 * np.linalg.norm(b)
+    xs = np.linalg.solve(A, b)
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+
+
+def test_cg_residuals_orthogonal_and_history():
+    m = synth.Mesh(2, 2, seed=3)
+    A = fem_ref.assemble(m, 1.0)
+    b = synth.uniform(m.NG, 13)
+    res = []
+    for j in range(8):
+        xj, it, al, be, rr = oracle.cg(m.E, 2, m.h, 1.0, m.ids, m.NG, b, maxit=j, fixed_iters=True)
+        assert it == j
+        res.append(b - A @ xj)
+        # recursively updated r.r agrees with the true residual
+        assert abs(rr[-1] - res[-1] @ res[-1]) <= 1e-10 * (b @ b)
+    for i in range(8):
+        for j in range(i + 1, 8):
+            ri, rj = res[i], res[j]
+            assert abs(ri @ rj) <= 1e-10 * np.linalg.norm(ri) * np.linalg.norm(rj)
+    # alpha, beta recomputed from the residual sequence (Algorithm 1)
+    _, _, al, be, rr = oracle.cg(m.E, 2, m.h, 1.0, m.ids, m.NG, b, maxit=6, fixed_iters=True)
+    for j in range(5):
+        assert abs(be[j] - (res[j + 1] @ res[j + 1]) / (res[j] @ res[j])) <= 1e-9 * be[j]
+
+
+def test_cg_matches_dense_solve():
+    m = synth.Mesh(2, 3, seed=6)
+    coef = synth.lognormal(m.E, 5)
+    A = fem_ref.assemble(m, 1.0, coef)
+    b = synth.uniform(m.NG, 14)
+    x, it, *_ = oracle.cg(m.E, 3, m.h, 1.0, m.ids, m.NG, b, tol=1e-12, maxit=2000, coef=coef)
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_pcg_jacobi_and_ir():
+    m = synth.Mesh(2, 3, seed=6)
+    coef = synth.lognormal(m.E, 5)
+    A = fem_ref.assemble(m, 1e-2, coef)
+    b = synth.uniform(m.NG, 15)
+    xs = np.linalg.solve(A, b)
+    x, it, rr = oracle.pcg_jacobi(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, tol=1e-12, maxit=2000, coef=coef)
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+    _, it_cg, *_ = oracle.cg(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, tol=1e-12, maxit=2000, coef=coef)
+    assert it < it_cg  # Jacobi helps on the lognormal coefficient field
+    x2, inner, outer, rel = oracle.cg_ir_f32(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, 1e-10, coef=coef)
+    assert rel <= 1e-10
+    assert np.linalg.norm(b - A @ x2) <= 2e-10 * np.linalg.norm(b)
+    assert outer >= 2  # FP32 alone cannot reach 1e-10
+
+
+# ------------------------------------------------------------------ performance model
+
+def _table2():
+    rows, fb = {}, {}
+    with open(os.path.join(GOLDEN, "table2_model_fits.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            t = line.split()
+            if t[0] == "FB":
+                fb[t[1]] = (float(t[2]), float(t[3]))
+            else:
+                v = list(map(float, t[1:]))
+                rows[t[0]] = {"R7": v[0:2], "TitanV": v[2:4], "MI60": v[4:6], "V100": v[6:8]}
+    return rows, fb
+
+
+def test_fischer_brown_matches_paper_text():
+    from paper_2009_10917_gb300 import perfmodel
+    rows, fb = _table2()
+    for gpu in ("V100", "MI60"):
+        T0_us, W = rows["BS3"][gpu]
+        B = perfmodel.fischer_brown(T0_us * 1e-6, W * 1e9)
+        mib, mdoubles = fb[gpu]
+        assert abs(B / 2 ** 20 - mib) <= 0.05 * mib          # within the fit's rounding
+        assert abs(B / 8 / 1e6 - mdoubles) <= 0.05 * mdoubles
+        assert abs(perfmodel.effective_bandwidth(B, T0_us * 1e-6, W * 1e9) / (W * 1e9) - 0.8) < 1e-12
+
+
+def test_model_fit_recovers_table2():
+    from paper_2009_10917_gb300 import perfmodel
+    rows, _ = _table2()
+    B = np.logspace(4, 10, 400)
+    for test, gpus in rows.items():
+        for gpu, (T0_us, W) in gpus.items():
+            T = perfmodel.time_model(B, T0_us * 1e-6, W * 1e9)
+            t0, w = perfmodel.fit(B, T)
+            assert abs(t0 - T0_us * 1e-6) < 1e-12 and abs(w / (W * 1e9) - 1) < 1e-9
