@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the Benchmark Streaming hot path on GB300.
+
+One step = the seven BS operations of Table 1 at the largest configuration
+of the streaming sweep: copy, AXPY, norm, inner product and the fused CG
+update on FP64 vectors of 2^28 entries (2 GiB each, far larger than L2), then
+scatter and gather on the degree-7, 48^3 structured hex mesh with permuted
+elements (110592 elements, 56.6M local and 38.3M global nodes).  `value` is
+the algorithmic bytes of the step (SURVEY-style counts: copy 16n, AXPY 24n,
+norm 8n, dot 16n, CG update 48n, scatter 12 N_L + 8 N_G, gather
+12 N_L + 12 N_G + 4) divided by the device time, i.e. the effective HBM GB/s
+of the whole step.  Per-operation GB/s and fractions of the measured HBM peak
+are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the path has no exchange step at these sizes, so N > 1 runs N
+independent replicas (weak scaling); value sums the bytes of all ranks over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "per-op HBM GB/s (% of GB300 peak); time-to-1e-8 CG solve, plain vs batched/learned"
+OPS = ["copy", "axpy", "norm", "dot", "cg_update", "scatter", "gather"]
+KERNEL_OF = {"copy": "k_copy", "axpy": "k_axpy", "norm": "k_dot", "dot": "k_dot",
+             "cg_update": "k_cg_update", "scatter": "k_scatter", "gather": "k_gather"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=28, help="vector length 2^k for BS1-BS5")
+    ap.add_argument("--mesh", default="7,48", help="N,K of the BS6/BS7 mesh")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def alg_bytes(n, NL, NG):
+    return {"copy": 16 * n, "axpy": 24 * n, "norm": 8 * n, "dot": 16 * n, "cg_update": 48 * n,
+            "scatter": 4 * NL + 8 * NG + 8 * NL, "gather": 8 * NL + 4 * NL + 4 * (NG + 1) + 8 * NG}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def config(args, n, N, K, NL, NG):
+    return {"workload": f"BS1-BS5 FP64 n=2^{args.log2n}; BS6/BS7 N={N} on {K}^3 hex mesh "
+                        f"(N_L={NL}, N_G={NG}), permuted elements",
+            "n": n, "degree": N, "mesh_K": K, "N_L": NL, "N_G": NG, "alpha": 0.5, "beta": 1.0,
+            "l2": "inputs larger than L2 (2 GiB vectors); no flush needed",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- inputs
+
+def make_inputs(args):
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2009_10917_gb300 import synth
+    n = 1 << args.log2n
+    N, K = (int(v) for v in args.mesh.split(","))
+    with ThreadPoolExecutor(8) as ex:
+        fut = {name: ex.submit(synth.uniform, n, 1, s)
+               for s, name in enumerate(["x", "p", "Ap", "xc", "r"])}
+        mesh = synth.Mesh(K, N, seed=1)
+        fut["qG"] = ex.submit(synth.uniform, mesh.NG, 2, 0)
+        host = {k: f.result() for k, f in fut.items()}
+    return n, mesh, host
+
+
+# ---------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2009_10917_gb300 import bs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n, mesh, host = make_inputs(args)
+    NL, NG = mesh.NL, mesh.NG
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    Z = bs.Map(mesh.E, mesh.N, NG, mesh.ids)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    qL = torch.empty(NL, dtype=torch.float64, device="cuda")
+    qG2 = torch.empty(NG, dtype=torch.float64, device="cuda")
+    red = torch.zeros(4, dtype=torch.float64, device="cuda")
+    ws = bs.workspace()
+    stream = torch.cuda.current_stream()
+
+    def step(d, ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        bs.copy(d["x"], y)
+        mark(1)
+        bs.axpy(0.5, d["x"], 1.0, y)
+        mark(2)
+        bs.norm(d["x"], red[0:2], ws)
+        mark(3)
+        bs.dot(d["x"], y, red[2:3], ws)
+        mark(4)
+        bs.cg_update(0.5, d["p"], d["Ap"], d["xc"], d["r"], red[3:4], ws)
+        mark(5)
+        Z.scatter(d["qG"], qL)
+        mark(6)
+        Z.gather(qL, qG2)
+        mark(7)
+
+    for _ in range(args.warmup):
+        step(dev)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0e.record(stream)
+        for k in range(args.steps):
+            step(dev, evs[k])
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    total_ms = t0e.elapsed_time(t1e)
+    per_op_ms = {op: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps
+                 for i, op in enumerate(OPS)}
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    B = alg_bytes(n, NL, NG)
+    step_bytes = sum(B.values())
+    value = world * step_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    per_op = {op: {"gbs": round(B[op] / (per_op_ms[op] * 1e-3) / 1e9, 1),
+                   "ms": round(per_op_ms[op], 4),
+                   "frac": round(B[op] / (per_op_ms[op] * 1e-3) / 1e9 / peak, 4),
+                   "frac_of_8000": round(B[op] / (per_op_ms[op] * 1e-3) / 1e9 / 8000.0, 4)}
+              for op in OPS}
+    dom = max(OPS, key=lambda op: per_op_ms[op])
+    achieved = B[dom] / (per_op_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": KERNEL_OF[dom], "op": dom,
+                "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic_for(KERNEL_OF[dom], dom)}
+
+    # end to end: pinned host inputs copied in and results read back every step
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+        out_h = torch.empty(4, dtype=torch.float64).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+
+        def e2e_step():
+            for k_, v in pinned.items():
+                dev[k_].copy_(v, non_blocking=True)
+            step(dev)
+            out_h.copy_(red, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ksteps = max(3, args.steps // 4)
+        a.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        b_.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = a.elapsed_time(b_)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": round(world * step_bytes * ksteps / (ems * 1e-3) / 1e9, 1), "unit": "GB/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 32, "steps": ksteps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config(args, n, mesh.N, mesh.K, NL, NG),
+                "per_op": per_op, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 7 * args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def traffic_for(kernel, op):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source has not changed since it was taken; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d["ops"][op]
+        from paper_2009_10917_gb300 import build
+        if ent.get("source_sha") != build.source_digest():
+            return None
+        return ent["dram_bytes_per_launch_full"]
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- oracle on the host
+
+def oracle_sample(seconds=10.0):
+    """Time the oracle on a bounded sample of the same workload: BS1-BS5 at
+    n = 2^22, BS6/BS7 on the degree-7, 16^3 mesh.  Returns (GB/s, detail)."""
+    import oracle
+    from paper_2009_10917_gb300 import synth
+    n = 1 << 22
+    x, p, Ap, xc, r = (synth.uniform(n, 1, s) for s in range(5))
+    mesh = synth.Mesh(16, 7, seed=1)
+    qG = synth.uniform(mesh.NG, 2)
+    B = alg_bytes(n, mesh.NL, mesh.NG)
+    oracle.lib()
+    reps, t = 0, 0.0
+    while t < seconds or reps < 1:
+        t0 = time.perf_counter()
+        y = oracle.copy(x)
+        y = oracle.axpy(0.5, x, 1.0, y)
+        oracle.norm(x)
+        oracle.dot(x, y)
+        xc, r, _ = oracle.cg_update(0.5, p, Ap, xc, r)
+        qL = oracle.scatter(mesh.ids, qG, __import__("numpy").zeros(mesh.NL))
+        oracle.gather(mesh.ids, qL, mesh.NG)
+        t += time.perf_counter() - t0
+        reps += 1
+    gbs = sum(B.values()) * reps / t / 1e9
+    return gbs, {"reps": reps, "seconds": round(t, 2),
+                 "sample": f"BS1-BS5 at n=2^22, BS6/BS7 on N=7 16^3 mesh, {reps} passes"}
+
+
+def cpu_baseline(args):
+    gbs, d = oracle_sample()
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": d["sample"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = 1 << args.log2n
+    N, K = (int(v) for v in args.mesh.split(","))
+    NL, NG = K ** 3 * (N + 1) ** 3, (K * N + 1) ** 3
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(1.0)
+    vals, t_all = [], 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        gbs, d = oracle_sample(2.0)
+        t_all += time.perf_counter() - t0
+        vals.append(gbs)
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * t_all / max(1, args.steps), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": config(args, n, N, K, NL, NG),
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1,
+                             "kind": "oracle", "sample": d["sample"]},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

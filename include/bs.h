@@ -1,0 +1,205 @@
+/*
+ * bs.h -- C ABI of libbs: the Benchmark Streaming operations (BS1-BS7) and
+ * the conjugate-gradient solve of Chalmers & Warburton, "Portable high-order
+ * finite element kernels I: Streaming Operations" (arXiv 2009.10917), built
+ * for NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Vectors are caller-owned DEVICE pointers on the current CUDA device,
+ *    contiguous, element i at ptr[i].  FP64 unless the name ends in _f32.
+ *    16-byte alignment enables the 128-bit path; other alignments are
+ *    accepted and take a scalar path.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *    call is asynchronous on that stream unless stated otherwise; results
+ *    written to device scalars are valid once the stream reaches them.
+ *  - Opaque objects (bs_workspace, bs_map, bs_problem) are owned by the
+ *    library, created on the current device and freed by *_destroy.  Host
+ *    arrays passed to *_create are copied; the caller keeps ownership.
+ *  - One bs_workspace may serve one stream at a time: reductions that share
+ *    a workspace must not overlap on the GPU.
+ *  - Every function returns a bs_status.  No C++ exception crosses the ABI.
+ *    bs_last_error() gives a thread-local description of the last failure.
+ *    Arguments are validated before any launch; on BS_ERR_ARG nothing was
+ *    enqueued.
+ *  - Sizes are int64_t counts of elements; n == 0 is valid and enqueues
+ *    nothing except the zero results of reductions.
+ */
+#ifndef BS_H_
+#define BS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+
+typedef enum {
+  BS_OK = 0,
+  BS_ERR_ARG = 1,            /* invalid argument; nothing enqueued          */
+  BS_ERR_CUDA = 2,           /* a CUDA runtime call failed                  */
+  BS_ERR_TIMEOUT = 3,        /* a bounded device-side wait ran out          */
+  BS_ERR_BREAKDOWN = 4,      /* CG breakdown: p.Ap <= 0 or not finite       */
+  BS_ERR_NOT_CONVERGED = 5,  /* iteration limit reached before tolerance    */
+  BS_ERR_DEVICE_CHECK = 6,   /* a device-side validity check failed         */
+  BS_ERR_ALLOC = 7           /* device or host allocation failed            */
+} bs_status;
+
+/* Static description of a status code. */
+const char *bs_error_string(int status);
+/* Thread-local detail of the most recent failing call on this thread. */
+const char *bs_last_error(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int bs_version(void);
+
+/* ------------------------------------------------------------ workspace */
+
+/* Scratch for single-launch reductions: per-block partial sums, an arrival
+ * counter and result slots (a few KB of device memory, cudaMalloc'd on the
+ * current device).  The counter is left at zero after every reduction. */
+typedef struct bs_workspace bs_workspace;
+int bs_workspace_create(bs_workspace **ws);
+int bs_workspace_destroy(bs_workspace *ws);
+
+/* ------------------------------------------------------------ BS1-BS5 */
+
+/* BS1, vector copy (Table 1; Listing 1): y[i] = x[i], i < n.  Bitwise. */
+int bs_copy(int64_t n, const double *x, double *y, void *stream);
+
+/* BS2, vector AXPY (Table 1; Listing 2): y[i] = fma(alpha, x[i], beta*y[i]),
+ * i.e. alpha*x + beta*y with the product beta*y rounded on its own and one
+ * fused multiply-add.  Bitwise reproducible; x and y must not overlap. */
+int bs_axpy(int64_t n, double alpha, const double *x, double beta, double *y,
+            void *stream);
+
+/* BS3, vector norm (Table 1; Listing 3): d_out[0] = x.x, d_out[1] =
+ * sqrt(x.x), written to DEVICE memory (2 doubles) in one launch.  The
+ * summation order is fixed by n and the device, so repeated calls are
+ * bitwise identical. */
+int bs_norm(int64_t n, const double *x, double *d_out, bs_workspace *ws,
+            void *stream);
+
+/* BS4, inner product (Table 1): d_out[0] = x.y (DEVICE, 1 double), one
+ * launch, deterministic as bs_norm. */
+int bs_dot(int64_t n, const double *x, const double *y, double *d_out,
+           bs_workspace *ws, void *stream);
+
+/* BS5, fused CG update (Table 1; Algorithm 1 steps 8-10 fused):
+ *   x[i] = fma(alpha, p[i], x[i]);  r[i] = fma(-alpha, Ap[i], r[i]);
+ *   d_rr[0] = sum of the updated r[i]^2   (DEVICE, 1 double)
+ * in one pass: x and r are read and written once, p and Ap read once. */
+int bs_cg_update(int64_t n, double alpha, const double *p, const double *Ap,
+                 double *x, double *r, double *d_rr, bs_workspace *ws,
+                 void *stream);
+
+/* FP32-storage twins (vectors of float).  Products and sums inside the
+ * reductions are carried as unevaluated pairs of floats (about 44 bits);
+ * the per-block partials are combined in double, and results are doubles. */
+int bs_copy_f32(int64_t n, const float *x, float *y, void *stream);
+int bs_axpy_f32(int64_t n, float alpha, const float *x, float beta, float *y,
+                void *stream);
+int bs_norm_f32(int64_t n, const float *x, double *d_out, bs_workspace *ws,
+                void *stream);
+int bs_dot_f32(int64_t n, const float *x, const float *y, double *d_out,
+               bs_workspace *ws, void *stream);
+int bs_cg_update_f32(int64_t n, float alpha, const float *p, const float *Ap,
+                     float *x, float *r, double *d_rr, bs_workspace *ws,
+                     void *stream);
+
+/* ------------------------------------------------------------ BS6, BS7 */
+
+/* The scatter operator Z (eq. scatter_def): an N_L x N_G Boolean matrix with
+ * one unit entry per row, given by the int32 local-to-global map
+ * h_l2g[l], l < N_L = E*(N+1)^3 (Sec. 5: "scatterIds").  h_l2g[l] < 0 masks
+ * local node l (Sec. 5: boundary conditions).  Every h_l2g[l] must be < NG.
+ * bs_map_create copies the map to the device and builds the CSR form of Z^T
+ * (Sec. 5, Listing 4): rowStarts[NG+1] and colIds[nnz], the local indices of
+ * each global node in ascending order.  Host-side, synchronous. */
+typedef struct bs_map bs_map;
+int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g,
+                  bs_map **map);
+int bs_map_destroy(bs_map *map);
+/* N_L, N_G and the number of unmasked local nodes (nnz of Z). */
+int bs_map_info(const bs_map *map, int64_t *NL, int64_t *NG, int64_t *nnz);
+/* Copy the CSR of Z^T back to host arrays rowStarts[NG+1], colIds[nnz]
+ * (synchronous; for verification). */
+int bs_map_export(const bs_map *map, int32_t *h_row_starts, int32_t *h_col_ids);
+/* Device valence diag(Z^T Z) into d_val[NG] (int32). */
+int bs_map_valence(const bs_map *map, int32_t *d_val, void *stream);
+
+/* BS7, scatter q_L = Z q_G (Table 1; Listing 5): qL[l] = qG[l2g[l]] for
+ * l2g[l] >= 0; masked entries of qL are left untouched.  Bitwise. */
+int bs_scatter(const bs_map *map, const double *qG, double *qL, void *stream);
+
+/* BS6, gather q_G = Z^T q_L (Table 1; Listing 4): qG[g] = sum of qL[l] over
+ * the local copies l of g, accumulated from +0.0 in ascending l (no atomics,
+ * bitwise reproducible).  A global node with no copies gets 0. */
+int bs_gather(const bs_map *map, const double *qL, double *qG, void *stream);
+
+int bs_scatter_f32(const bs_map *map, const float *qG, float *qL, void *stream);
+int bs_gather_f32(const bs_map *map, const float *qL, float *qG, void *stream);
+
+/* ------------------------------------------------------------ operator */
+
+/* The Helmholtz operator A = Z^T (S_L + lambda M_L) Z of eqs. global_system,
+ * assembled_stiff and assembled_mass, discretised with degree-N GLL
+ * Lagrange bases on affine cube elements of side h (Sec. 2, eq. basis),
+ * collocated GLL quadrature (lumped mass):
+ *   (A_e u)_ijk = c_e (h/2) [ (K x W x W) + (W x K x W) + (W x W x K) ] u
+ *               + lambda (h/2)^3 w_i w_j w_k u_ijk,   K = D^T W D,
+ * with c_e = h_coef[e] (or 1 when h_coef is NULL).  Local node (i,j,k) of
+ * element e is l = e*(N+1)^3 + i + (N+1)(j + (N+1)k).  The problem keeps a
+ * reference to `map` (which must outlive it) and owns its device scratch
+ * (two N_L and six N_G vectors).  Host-side, synchronous. */
+typedef struct bs_problem bs_problem;
+int bs_problem_create(const bs_map *map, double h, double lambda,
+                      const double *h_coef, bs_problem **prob);
+int bs_problem_destroy(bs_problem *prob);
+
+/* Ap = A p (N_G vectors). */
+int bs_apply_A(const bs_problem *prob, const double *p, double *Ap,
+               void *stream);
+/* Element-local A_L uL (N_L vectors; no Z, no Z^T). */
+int bs_apply_local(const bs_problem *prob, const double *uL, double *AuL,
+                   void *stream);
+/* diag(A) = Z^T diag(A_L) into d_diag[NG]. */
+int bs_diag_A(const bs_problem *prob, double *d_diag, void *stream);
+
+/* ------------------------------------------------------------ CG */
+
+enum {
+  BS_CG_FIXED_ITERS = 1, /* run exactly maxit iterations                   */
+  BS_CG_JACOBI = 2,      /* Jacobi preconditioner z = diag(A)^-1 r         */
+  BS_CG_GRAPH = 4,       /* replay the iteration as a captured CUDA graph  */
+  BS_CG_X0 = 8           /* x holds the initial guess (else x0 = 0)        */
+};
+
+typedef struct {
+  int32_t iterations;   /* CG iterations performed                        */
+  int32_t status;       /* bs_status of the solve                         */
+  int32_t outer;        /* refinement steps (bs_cg_solve_refined_f32)     */
+  int32_t reserved;
+  double rr;            /* final r.r (recursive residual)                 */
+  double bb;            /* b.b                                            */
+  double rel_residual;  /* sqrt(rr / bb); FP64 true residual when refined */
+  double seconds;       /* wall time of the solve on the host             */
+} bs_cg_info;
+
+/* Algorithm 1 on A x = b (N_G vectors b, x).  Stops when r.r <= tol^2 b.b or
+ * after maxit iterations; the convergence flag is computed on the device and
+ * read back every few iterations.  d_hist (DEVICE, may be NULL) receives
+ * 3*(maxit+1) doubles: alpha_j at [3j], beta_j at [3j+1], r_{j+1}.r_{j+1} at
+ * [3j+2].  Synchronises `stream` before returning; info (host) may be NULL.
+ * Returns BS_ERR_NOT_CONVERGED if maxit is reached without BS_CG_FIXED_ITERS,
+ * BS_ERR_BREAKDOWN on p.Ap <= 0. */
+int bs_cg_solve(const bs_problem *prob, const double *b, double *x, double tol,
+                int32_t maxit, int32_t flags, double *d_hist,
+                bs_cg_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BS_H_ */

@@ -61,6 +61,12 @@ _SIGS = {
     "bso_gather": (None, [_i64, _i64, _I, _D, _D]),
     "bso_valence": (None, [_i64, _i64, _I, _I]),
     "bso_gll": (_int, [_int, _D, _D, _D]),
+    "bso_csr": (None, [_i64, _i64, _I, _I, _I]),
+    "bso_axpy_f32": (None, [_i64, ctypes.c_float, _F, ctypes.c_float, _F]),
+    "bso_dot_f32": (_dbl, [_i64, _F, _F]),
+    "bso_cg_update_f32": (_dbl, [_i64, ctypes.c_float, _F, _F, _F, _F]),
+    "bso_scatter_f32": (None, [_i64, _I, _F, _F]),
+    "bso_gather_f32": (None, [_i64, _i64, _I, _F, _F]),
     "bso_apply_A": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D]),
     "bso_apply_local": (_int, [_int, _int, _dbl, _dbl, _D, _D, _D]),
     "bso_diag_A": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D]),
@@ -170,6 +176,58 @@ def valence(ids, NG):
     v = np.empty(int(NG), dtype=np.int32)
     lib().bso_valence(ids.size, int(NG), _i(ids), _i(v))
     return v
+
+
+def csr(ids, NG):
+    """CSR of Z^T by definition: (rowStarts[NG+1], colIds ascending per row)."""
+    ids = _ids(ids)
+    rs = np.empty(int(NG) + 1, dtype=np.int32)
+    ci = np.empty(max(int((ids >= 0).sum()), 1), dtype=np.int32)
+    lib().bso_csr(ids.size, int(NG), _i(ids), _i(rs), _i(ci))
+    return rs, ci[:int((ids >= 0).sum())]
+
+
+# ---------------------------------------------------------------- FP32 twins
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fp(a):
+    return a.ctypes.data_as(_F)
+
+
+def axpy_f32(alpha, x, beta, y):
+    """BS2 in float: fmaf(alpha, x, beta*y)."""
+    x, y = _f32(x), _f32(y).copy()
+    lib().bso_axpy_f32(x.size, float(alpha), _fp(x), float(beta), _fp(y))
+    return y
+
+
+def dot_f32(x, y):
+    """Sum of products of float vectors, exact products, Dot2 summation."""
+    x, y = _f32(x), _f32(y)
+    return float(lib().bso_dot_f32(x.size, _fp(x), _fp(y)))
+
+
+def cg_update_f32(alpha, p, Ap, x, r):
+    """BS5 in float; returns (x', r', r'.r')."""
+    p, Ap, x, r = _f32(p), _f32(Ap), _f32(x).copy(), _f32(r).copy()
+    rr = lib().bso_cg_update_f32(x.size, float(alpha), _fp(p), _fp(Ap), _fp(x), _fp(r))
+    return x, r, float(rr)
+
+
+def scatter_f32(ids, qG, qL_init):
+    ids, qG, qL = _ids(ids), _f32(qG), _f32(qL_init).copy()
+    lib().bso_scatter_f32(ids.size, _i(ids), _fp(qG), _fp(qL))
+    return qL
+
+
+def gather_f32(ids, qL, NG):
+    ids, qL = _ids(ids), _f32(qL)
+    qG = np.empty(int(NG), dtype=np.float32)
+    lib().bso_gather_f32(ids.size, int(NG), _i(ids), _fp(qL), _fp(qG))
+    return qG
 
 
 # ---------------------------------------------------------------- operator

@@ -537,3 +537,65 @@ int bso_cg_ir_f32(int E, int N, double h, double lambda, const double *coef,
   free(fb);
   return total;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The CSR form of Z^T (Sec. 5, Listing 4), by its definition:              */
+/* rowStarts[g] = #{l : 0 <= ids[l] < g}; colIds lists, row by row, the     */
+/* local indices l with ids[l] = g in ascending order.                      */
+/* ------------------------------------------------------------------------ */
+void bso_csr(int64_t NL, int64_t NG, const int32_t *ids, int32_t *row_starts,
+             int32_t *col_ids) {
+  for (int64_t g = 0; g <= NG; ++g) row_starts[g] = 0;
+  for (int64_t l = 0; l < NL; ++l)
+    if (ids[l] >= 0) row_starts[ids[l] + 1] += 1;
+  for (int64_t g = 0; g < NG; ++g) row_starts[g + 1] += row_starts[g];
+  /* rows in order, each row's l ascending: one stable bucket pass */
+  int32_t *next = malloc(sizeof(int32_t) * (size_t)(NG > 0 ? NG : 1));
+  if (!next) return;
+  for (int64_t g = 0; g < NG; ++g) next[g] = row_starts[g];
+  for (int64_t l = 0; l < NL; ++l)
+    if (ids[l] >= 0) col_ids[next[ids[l]]++] = (int32_t)l;
+  free(next);
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32-storage twins of BS2, BS5, BS6, BS7: the same definitions with      */
+/* float values and fmaf; the r.r of BS5 is the Dot2 sum of the updated     */
+/* float values taken as doubles (their products are exact in double).     */
+/* ------------------------------------------------------------------------ */
+void bso_axpy_f32(int64_t n, float alpha, const float *x, float beta, float *y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = fmaf(alpha, x[i], beta * y[i]);
+}
+
+double bso_dot_f32(int64_t n, const float *x, const float *y) {
+  if (n <= 0) return 0.0;
+  double p, s, h, r, q;
+  two_prod((double)x[0], (double)y[0], &p, &s);
+  for (int64_t i = 1; i < n; ++i) {
+    two_prod((double)x[i], (double)y[i], &h, &r);
+    two_sum(p, h, &p, &q);
+    s = s + (q + r);
+  }
+  return p + s;
+}
+
+double bso_cg_update_f32(int64_t n, float alpha, const float *p, const float *Ap,
+                         float *x, float *r) {
+  for (int64_t i = 0; i < n; ++i) {
+    x[i] = fmaf(alpha, p[i], x[i]);
+    r[i] = fmaf(-alpha, Ap[i], r[i]);
+  }
+  return bso_dot_f32(n, r, r);
+}
+
+void bso_scatter_f32(int64_t NL, const int32_t *ids, const float *qG, float *qL) {
+  for (int64_t l = 0; l < NL; ++l)
+    if (ids[l] >= 0) qL[l] = qG[ids[l]];
+}
+
+void bso_gather_f32(int64_t NL, int64_t NG, const int32_t *ids, const float *qL,
+                    float *qG) {
+  for (int64_t g = 0; g < NG; ++g) qG[g] = 0.0f;
+  for (int64_t l = 0; l < NL; ++l)
+    if (ids[l] >= 0) qG[ids[l]] = qG[ids[l]] + qL[l];
+}

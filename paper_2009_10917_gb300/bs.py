@@ -1,0 +1,324 @@
+"""Thin Python binding of libbs (include/bs.h) over torch CUDA tensors.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors must be contiguous CUDA tensors on the current device; calls are
+enqueued on torch's current stream.  There is no CPU fallback: if libbs.so
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+BS_OK = 0
+BS_ERR_ARG = 1
+BS_ERR_CUDA = 2
+BS_ERR_TIMEOUT = 3
+BS_ERR_BREAKDOWN = 4
+BS_ERR_NOT_CONVERGED = 5
+BS_ERR_DEVICE_CHECK = 6
+BS_ERR_ALLOC = 7
+
+BS_CG_FIXED_ITERS = 1
+BS_CG_JACOBI = 2
+BS_CG_GRAPH = 4
+BS_CG_X0 = 8
+
+
+class BSError(RuntimeError):
+    def __init__(self, status, fn, detail):
+        super().__init__(f"{fn}: status {status} ({detail})")
+        self.status = status
+
+
+class CgInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("outer", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rr", ctypes.c_double), ("bb", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_d = ctypes.c_double
+_f = ctypes.c_float
+_pp = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "bs_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "bs_last_error": (ctypes.c_char_p, []),
+    "bs_version": (ctypes.c_int, []),
+    "bs_workspace_create": (ctypes.c_int, [_pp]),
+    "bs_workspace_destroy": (ctypes.c_int, [_vp]),
+    "bs_copy": (ctypes.c_int, [_i64, _vp, _vp, _vp]),
+    "bs_axpy": (ctypes.c_int, [_i64, _d, _vp, _d, _vp, _vp]),
+    "bs_norm": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp]),
+    "bs_dot": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
+    "bs_cg_update": (ctypes.c_int, [_i64, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bs_copy_f32": (ctypes.c_int, [_i64, _vp, _vp, _vp]),
+    "bs_axpy_f32": (ctypes.c_int, [_i64, _f, _vp, _f, _vp, _vp]),
+    "bs_norm_f32": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp]),
+    "bs_dot_f32": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
+    "bs_cg_update_f32": (ctypes.c_int, [_i64, _f, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bs_map_create": (ctypes.c_int, [_i32, _i32, _i64, _vp, _pp]),
+    "bs_map_destroy": (ctypes.c_int, [_vp]),
+    "bs_map_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                   ctypes.POINTER(_i64)]),
+    "bs_map_export": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bs_map_valence": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bs_scatter": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_gather": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_scatter_f32": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_gather_f32": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_problem_create": (ctypes.c_int, [_vp, _d, _d, _vp, _pp]),
+    "bs_problem_destroy": (ctypes.c_int, [_vp]),
+    "bs_apply_A": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_apply_local": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_diag_A": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bs_cg_solve": (ctypes.c_int, [_vp, _vp, _vp, _d, _i32, _i32, _vp,
+                                   ctypes.POINTER(CgInfo), _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libbs.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if _build.is_stale():
+                try:
+                    path = _build.build()
+                except Exception as exc:  # no nvcc or failed build: no fallback
+                    if not os.path.exists(path):
+                        raise RuntimeError(f"libbs.so is missing and cannot be built: {exc}")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, fn):
+    if rc != BS_OK:
+        L = lib()
+        raise BSError(rc, fn, L.bs_last_error().decode(errors="replace"))
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=torch.float64, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Workspace:
+    """Reduction scratch of the current device (bs_workspace)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().bs_workspace_create(ctypes.byref(h)), "bs_workspace_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bs_workspace_destroy(self.handle)
+            self.handle = None
+
+
+_ws = {}
+
+
+def workspace() -> Workspace:
+    """The default workspace of the current device (one per device)."""
+    dev = torch.cuda.current_device()
+    if dev not in _ws:
+        _ws[dev] = Workspace()
+    return _ws[dev]
+
+
+# ---------------------------------------------------------------- BS1-BS5
+
+def _sfx(t):
+    return "_f32" if t.dtype == torch.float32 else ""
+
+
+def copy(x, y=None):
+    """BS1: y = x."""
+    y = torch.empty_like(x) if y is None else y
+    _check(getattr(lib(), "bs_copy" + _sfx(x))(x.numel(), _ptr(x, x.dtype, "x"),
+                                               _ptr(y, x.dtype, "y"), _stream()), "bs_copy")
+    return y
+
+
+def axpy(alpha, x, beta, y):
+    """BS2: y = fma(alpha, x, beta*y), in place on y."""
+    _check(getattr(lib(), "bs_axpy" + _sfx(x))(x.numel(), alpha, _ptr(x, x.dtype, "x"), beta,
+                                               _ptr(y, x.dtype, "y"), _stream()), "bs_axpy")
+    return y
+
+
+def norm(x, out=None, ws=None):
+    """BS3: device tensor [x.x, sqrt(x.x)] (float64)."""
+    out = torch.empty(2, dtype=torch.float64, device=x.device) if out is None else out
+    ws = ws or workspace()
+    _check(getattr(lib(), "bs_norm" + _sfx(x))(x.numel(), _ptr(x, x.dtype, "x"), _ptr(out),
+                                               ws.handle, _stream()), "bs_norm")
+    return out
+
+
+def dot(x, y, out=None, ws=None):
+    """BS4: device tensor [x.y] (float64)."""
+    out = torch.empty(1, dtype=torch.float64, device=x.device) if out is None else out
+    ws = ws or workspace()
+    _check(getattr(lib(), "bs_dot" + _sfx(x))(x.numel(), _ptr(x, x.dtype, "x"),
+                                              _ptr(y, x.dtype, "y"), _ptr(out), ws.handle,
+                                              _stream()), "bs_dot")
+    return out
+
+
+def cg_update(alpha, p, Ap, x, r, out=None, ws=None):
+    """BS5: x += alpha p; r -= alpha Ap (in place); device tensor [r.r]."""
+    out = torch.empty(1, dtype=torch.float64, device=x.device) if out is None else out
+    ws = ws or workspace()
+    t = x.dtype
+    _check(getattr(lib(), "bs_cg_update" + _sfx(x))(
+        x.numel(), alpha, _ptr(p, t, "p"), _ptr(Ap, t, "Ap"), _ptr(x, t, "x"), _ptr(r, t, "r"),
+        _ptr(out), ws.handle, _stream()), "bs_cg_update")
+    return out
+
+
+# ---------------------------------------------------------------- BS6/BS7
+
+class Map:
+    """The scatter operator Z from an int32 local-to-global map (bs_map)."""
+
+    def __init__(self, E: int, N: int, NG: int, l2g: np.ndarray):
+        l2g = np.ascontiguousarray(l2g, dtype=np.int32)
+        Np = (N + 1) ** 3
+        if l2g.size != E * Np:
+            raise ValueError("l2g must have E*(N+1)^3 entries")
+        h = ctypes.c_void_p()
+        _check(lib().bs_map_create(E, N, NG, l2g.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(h)), "bs_map_create")
+        self.handle, self.E, self.N, self.NG, self.NL = h, E, N, NG, E * Np
+        nl, ng, nnz = _i64(), _i64(), _i64()
+        _check(lib().bs_map_info(h, ctypes.byref(nl), ctypes.byref(ng), ctypes.byref(nnz)),
+               "bs_map_info")
+        self.nnz = nnz.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bs_map_destroy(self.handle)
+            self.handle = None
+
+    def export(self):
+        rs = np.empty(self.NG + 1, dtype=np.int32)
+        ci = np.empty(max(self.nnz, 1), dtype=np.int32)
+        _check(lib().bs_map_export(self.handle, rs.ctypes.data_as(ctypes.c_void_p),
+                                   ci.ctypes.data_as(ctypes.c_void_p)), "bs_map_export")
+        return rs, ci[:self.nnz]
+
+    def valence(self, device=None):
+        out = torch.empty(self.NG, dtype=torch.int32, device=device or "cuda")
+        _check(lib().bs_map_valence(self.handle, _ptr(out, torch.int32), _stream()),
+               "bs_map_valence")
+        return out
+
+    def scatter(self, qG, qL=None):
+        """BS7: qL = Z qG (masked entries of qL untouched)."""
+        qL = torch.empty(self.NL, dtype=qG.dtype, device=qG.device) if qL is None else qL
+        _check(getattr(lib(), "bs_scatter" + _sfx(qG))(self.handle, _ptr(qG, qG.dtype, "qG"),
+                                                       _ptr(qL, qG.dtype, "qL"), _stream()),
+               "bs_scatter")
+        return qL
+
+    def gather(self, qL, qG=None):
+        """BS6: qG = Z^T qL."""
+        qG = torch.empty(self.NG, dtype=qL.dtype, device=qL.device) if qG is None else qG
+        _check(getattr(lib(), "bs_gather" + _sfx(qL))(self.handle, _ptr(qL, qL.dtype, "qL"),
+                                                      _ptr(qG, qL.dtype, "qG"), _stream()),
+               "bs_gather")
+        return qG
+
+
+# ---------------------------------------------------------------- operator and CG
+
+class Problem:
+    """A = Z^T (c S_L + lambda M_L) Z on a map (bs_problem)."""
+
+    def __init__(self, m: Map, h: float, lam: float, coef=None):
+        self.map = m  # keep the map alive
+        self.h, self.lam = h, lam
+        c = None
+        if coef is not None:
+            self._coef = np.ascontiguousarray(coef, dtype=np.float64)
+            c = self._coef.ctypes.data_as(ctypes.c_void_p)
+        hd = ctypes.c_void_p()
+        _check(lib().bs_problem_create(m.handle, h, lam, c, ctypes.byref(hd)),
+               "bs_problem_create")
+        self.handle = hd
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bs_problem_destroy(self.handle)
+            self.handle = None
+
+    def apply_A(self, p, Ap=None):
+        Ap = torch.empty_like(p) if Ap is None else Ap
+        _check(lib().bs_apply_A(self.handle, _ptr(p), _ptr(Ap), _stream()), "bs_apply_A")
+        return Ap
+
+    def apply_local(self, uL, AuL=None):
+        AuL = torch.empty_like(uL) if AuL is None else AuL
+        _check(lib().bs_apply_local(self.handle, _ptr(uL), _ptr(AuL), _stream()),
+               "bs_apply_local")
+        return AuL
+
+    def diag(self, device=None):
+        d = torch.empty(self.map.NG, dtype=torch.float64, device=device or "cuda")
+        _check(lib().bs_diag_A(self.handle, _ptr(d), _stream()), "bs_diag_A")
+        return d
+
+    def cg(self, b, x=None, tol=1e-8, maxit=1000, flags=0, hist=None, check=True):
+        """Algorithm 1.  Returns (x, info dict); hist (device, 3*(maxit+1))
+        receives alpha_j, beta_j, rr_{j+1}."""
+        if x is None:
+            x = torch.zeros_like(b)
+        info = CgInfo()
+        rc = lib().bs_cg_solve(self.handle, _ptr(b), _ptr(x), tol, maxit, flags,
+                               _ptr(hist) if hist is not None else None, ctypes.byref(info),
+                               _stream())
+        if check and rc not in (BS_OK,):
+            _check(rc, "bs_cg_solve")
+        d = info.as_dict()
+        d["rc"] = rc
+        return x, d

@@ -1,0 +1,160 @@
+// bs_gs.cu -- the scatter operator Z (eq. scatter_def) as a map object, and
+// the C ABI entry points of BS6 (gather) and BS7 (scatter).
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "bs_gs.cuh"
+
+namespace bs {
+
+__global__ void k_valence(int64_t NG, const int32_t *__restrict__ row_starts,
+                          int32_t *__restrict__ val) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = tid; g < NG; g += nth) val[g] = row_starts[g + 1] - row_starts[g];
+}
+
+static int check_map(const bs_map *m, const char *fn) {
+  if (!m) return fail(BS_ERR_ARG, "%s: map is NULL", fn);
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != m->device)
+    return fail(BS_ERR_ARG, "%s: map belongs to device %d, current is %d", fn, m->device, dev);
+  return BS_OK;
+}
+
+static void free_map(bs_map *m) {
+  if (!m) return;
+  cudaFree(m->d_ids);
+  cudaFree(m->d_row_starts);
+  cudaFree(m->d_col_ids);
+  free(m);
+}
+
+template <typename T>
+static int do_scatter(const bs_map *m, const T *qG, T *qL, void *stream, const char *fn) {
+  if (int rc = check_map(m, fn)) return rc;
+  if (m->NL == 0) return BS_OK;
+  BS_ARG(qL != nullptr && (qG != nullptr || m->NG == 0), "%s: NULL vector", fn);
+  return launch_scatter<T>(m, qG, qL, as_stream(stream));
+}
+
+template <typename T>
+static int do_gather(const bs_map *m, const T *qL, T *qG, void *stream, const char *fn) {
+  if (int rc = check_map(m, fn)) return rc;
+  if (m->NG == 0) return BS_OK;
+  BS_ARG(qG != nullptr && (qL != nullptr || m->NL == 0), "%s: NULL vector", fn);
+  return launch_gather<T, false, EpNone>(m, qL, qG, nullptr, nullptr, nullptr, EpNone{},
+                                         nullptr, as_stream(stream));
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map **out) {
+  BS_ARG(out != nullptr, "bs_map_create: out is NULL");
+  *out = nullptr;
+  BS_ARG(E >= 0 && N >= 1 && N <= 15, "bs_map_create: need E >= 0 and 1 <= N <= 15");
+  BS_ARG(NG >= 0 && NG < INT32_MAX, "bs_map_create: NG out of int32 range");
+  const int64_t Np = (int64_t)(N + 1) * (N + 1) * (N + 1);
+  const int64_t NL = (int64_t)E * Np;
+  BS_ARG(NL < INT32_MAX, "bs_map_create: N_L out of int32 range");
+  BS_ARG(NL == 0 || h_l2g != nullptr, "bs_map_create: map is NULL");
+  // counts per global node (and validation) -- the valence, diag(Z^T Z)
+  std::vector<int32_t> rs((size_t)NG + 1, 0);
+  int64_t nnz = 0;
+  for (int64_t l = 0; l < NL; ++l) {
+    const int32_t id = h_l2g[l];
+    if (id < 0) continue;
+    if (id >= NG) return fail(BS_ERR_ARG, "bs_map_create: l2g[%lld] = %d >= NG", (long long)l, id);
+    ++rs[(size_t)id + 1];
+    ++nnz;
+  }
+  for (int64_t g = 0; g < NG; ++g) rs[(size_t)g + 1] += rs[(size_t)g];
+  // stable placement: ascending l within each row
+  std::vector<int32_t> col((size_t)nnz);
+  {
+    std::vector<int32_t> fill(rs.begin(), rs.end() - 1);
+    for (int64_t l = 0; l < NL; ++l) {
+      const int32_t id = h_l2g[l];
+      if (id >= 0) col[(size_t)fill[(size_t)id]++] = (int32_t)l;
+    }
+  }
+  bs_map *m = (bs_map *)calloc(1, sizeof(bs_map));
+  if (!m) return fail(BS_ERR_ALLOC, "bs_map_create: host allocation");
+  m->E = E;
+  m->N = N;
+  m->NL = NL;
+  m->NG = NG;
+  m->nnz = nnz;
+  cudaError_t e = cudaGetDevice(&m->device);
+  // +4 elements of padding so 128-bit loads of the map never leave the buffer
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_ids, sizeof(int32_t) * (NL + 4));
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_row_starts, sizeof(int32_t) * (NG + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_col_ids, sizeof(int32_t) * (nnz + 4));
+  if (e == cudaSuccess && NL)
+    e = cudaMemcpy(m->d_ids, h_l2g, sizeof(int32_t) * NL, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_row_starts, rs.data(), sizeof(int32_t) * (NG + 1),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnz)
+    e = cudaMemcpy(m->d_col_ids, col.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_map(m);
+    return fail(BS_ERR_CUDA, "bs_map_create: %s", cudaGetErrorString(e));
+  }
+  *out = m;
+  return BS_OK;
+}
+
+int bs_map_destroy(bs_map *m) {
+  free_map(m);
+  return BS_OK;
+}
+
+int bs_map_info(const bs_map *m, int64_t *NL, int64_t *NG, int64_t *nnz) {
+  BS_ARG(m != nullptr, "bs_map_info: map is NULL");
+  if (NL) *NL = m->NL;
+  if (NG) *NG = m->NG;
+  if (nnz) *nnz = m->nnz;
+  return BS_OK;
+}
+
+int bs_map_export(const bs_map *m, int32_t *h_row_starts, int32_t *h_col_ids) {
+  if (int rc = check_map(m, "bs_map_export")) return rc;
+  if (h_row_starts)
+    BS_CUDA_TRY(cudaMemcpy(h_row_starts, m->d_row_starts, sizeof(int32_t) * (m->NG + 1),
+                           cudaMemcpyDeviceToHost));
+  if (h_col_ids && m->nnz)
+    BS_CUDA_TRY(cudaMemcpy(h_col_ids, m->d_col_ids, sizeof(int32_t) * m->nnz,
+                           cudaMemcpyDeviceToHost));
+  return BS_OK;
+}
+
+int bs_map_valence(const bs_map *m, int32_t *d_val, void *stream) {
+  if (int rc = check_map(m, "bs_map_valence")) return rc;
+  if (m->NG == 0) return BS_OK;
+  BS_ARG(d_val != nullptr, "bs_map_valence: NULL output");
+  const int grid = stream_grid(m->NG, 1, kStreamBlock, 8);
+  k_valence<<<grid, kStreamBlock, 0, as_stream(stream)>>>(m->NG, m->d_row_starts, d_val);
+  BS_LAUNCH_CHECK();
+  return BS_OK;
+}
+
+int bs_scatter(const bs_map *m, const double *qG, double *qL, void *stream) {
+  return do_scatter<double>(m, qG, qL, stream, "bs_scatter");
+}
+int bs_scatter_f32(const bs_map *m, const float *qG, float *qL, void *stream) {
+  return do_scatter<float>(m, qG, qL, stream, "bs_scatter_f32");
+}
+int bs_gather(const bs_map *m, const double *qL, double *qG, void *stream) {
+  return do_gather<double>(m, qL, qG, stream, "bs_gather");
+}
+int bs_gather_f32(const bs_map *m, const float *qL, float *qG, void *stream) {
+  return do_gather<float>(m, qL, qG, stream, "bs_gather_f32");
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// bs_op.cuh -- the Helmholtz operator A = Z^T (c S_L + lambda M_L) Z of
+// eqs. global_system, assembled_stiff, assembled_mass on affine cube
+// elements with degree-N GLL bases (Sec. 2) and collocated quadrature.
+//
+// Per element, with K = D^T W D (the 1-D GLL stiffness, exact because the
+// integrand has degree 2N-2), the stiffness is a sum of three one-directional
+// contractions:
+//   (S_e u)_ijk = (h/2) [ w_j w_k sum_m K_im u_mjk
+//                       + w_i w_k sum_m K_jm u_imk
+//                       + w_i w_j sum_m K_km u_ijm ],
+// 3(N+1) fused multiply-adds per node, and the lumped mass is diagonal,
+// (h/2)^3 w_i w_j w_k.  The kernel maps one thread to a column (i, j) of an
+// element and walks k, keeping the column in registers; the element sits in
+// shared memory.  Reading the input through the map (GATHER_IN) fuses the
+// scatter Z p into the same pass, so the N_L-sized Z p is never stored.
+#pragma once
+
+#include "bs_gs.cuh"
+
+namespace bs {
+
+constexpr int kMaxNq = 16;  // degrees 1..15
+
+// Per-problem constant tables, in device memory.
+template <typename T>
+struct OpTab {
+  T K[kMaxNq * kMaxNq];  // K[i*Nq + m] = (D^T W D)_im
+  T w[kMaxNq];           // GLL weights
+};
+
+template <int NQ>
+struct OpShape {
+  static constexpr int NQ2 = NQ * NQ;
+  static constexpr int NP = NQ * NQ * NQ;
+  static constexpr int EPB = NQ2 >= 128 ? 1 : 256 / NQ2;  // elements per block
+  static constexpr int THREADS = ((EPB * NQ2 + 31) / 32) * 32;
+};
+
+// out = A_L in  on E elements.  GATHER_IN: in is a global vector read
+// through ids (masked nodes read as 0); else in is element-local.
+// g = c-independent stiffness factor h/2, mlam = lambda (h/2)^3.
+template <typename T, int NQ, bool GATHER_IN>
+__global__ void __launch_bounds__(OpShape<NQ>::THREADS)
+    k_ax_local(int64_t E, const int32_t *__restrict__ ids, const T *__restrict__ in,
+               T *__restrict__ out, const OpTab<T> *__restrict__ tab,
+               const double *__restrict__ coef, T g, T mlam, const CgState *st) {
+  using S = OpShape<NQ>;
+  __shared__ T s_u[S::EPB][S::NP];
+  __shared__ T s_K[NQ * NQ];
+  __shared__ T s_w[NQ];
+  if (cg_halted(st)) return;
+  for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) s_K[t] = tab->K[(t / NQ) * NQ + t % NQ];
+  for (int t = threadIdx.x; t < NQ; t += blockDim.x) s_w[t] = tab->w[t];
+  const int le = threadIdx.x / S::NQ2;
+  const int ij = threadIdx.x - le * S::NQ2;
+  const int i = ij % NQ, j = ij / NQ;
+  const int64_t e = (int64_t)blockIdx.x * S::EPB + le;
+  const bool active = le < S::EPB && e < E;
+  T ureg[NQ];
+  if (active) {
+    const int64_t base = e * S::NP + ij;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      T u;
+      if (GATHER_IN) {
+        const int32_t id = __ldcs(ids + base + k * S::NQ2);
+        u = id >= 0 ? in[id] : T(0);
+      } else {
+        u = __ldcs(in + base + k * S::NQ2);
+      }
+      ureg[k] = u;
+      s_u[le][ij + k * S::NQ2] = u;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const T c = coef ? T(coef[e]) : T(1);
+  const T cg = c * g;
+  const T wi = s_w[i], wj = s_w[j];
+  const T wij = wi * wj;
+  const T *u = s_u[le];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    T ar = T(0), as = T(0), at = T(0);
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      ar = fmaT(s_K[i * NQ + m], u[m + NQ * j + S::NQ2 * k], ar);
+      as = fmaT(s_K[j * NQ + m], u[i + NQ * m + S::NQ2 * k], as);
+      at = fmaT(s_K[k * NQ + m], ureg[m], at);
+    }
+    const T wk = s_w[k];
+    T stiff = (wj * wk) * ar;
+    stiff = fmaT(wi * wk, as, stiff);
+    stiff = fmaT(wij, at, stiff);
+    const T mass = mlam * (wij * wk) * ureg[k];
+    __stcs(out + e * S::NP + ij + k * S::NQ2, fmaT(cg, stiff, mass));
+  }
+}
+
+template <typename T, bool GATHER_IN>
+int launch_ax_local(int N, int64_t E, const int32_t *ids, const T *in, T *out,
+                    const OpTab<T> *tab, const double *coef, T g, T mlam,
+                    const CgState *st, cudaStream_t s) {
+  if (E == 0) return BS_OK;
+#define BS_AX_CASE(NQ)                                                                   \
+  case NQ: {                                                                             \
+    using Sh = OpShape<NQ>;                                                              \
+    const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                    \
+    k_ax_local<T, NQ, GATHER_IN><<<(unsigned)grid, Sh::THREADS, 0, s>>>(E, ids, in, out, \
+                                                                       tab, coef, g,    \
+                                                                       mlam, st);       \
+    break;                                                                               \
+  }
+  switch (N + 1) {
+    BS_AX_CASE(2)
+    BS_AX_CASE(3)
+    BS_AX_CASE(4)
+    BS_AX_CASE(5)
+    BS_AX_CASE(6)
+    BS_AX_CASE(7)
+    BS_AX_CASE(8)
+    BS_AX_CASE(9)
+    BS_AX_CASE(10)
+    BS_AX_CASE(11)
+    BS_AX_CASE(12)
+    BS_AX_CASE(13)
+    BS_AX_CASE(14)
+    BS_AX_CASE(15)
+    BS_AX_CASE(16)
+    default:
+      return fail(BS_ERR_ARG, "degree %d unsupported", N);
+  }
+#undef BS_AX_CASE
+  BS_LAUNCH_CHECK();
+  return BS_OK;
+}
+
+}  // namespace bs
+
+// A problem: the map, the geometry and the device scratch of the solvers.
+struct bs_problem {
+  int device;
+  const bs_map *map;
+  int32_t N;
+  double h, lambda;
+  double *d_coef;                 // [E] or NULL
+  bs::OpTab<double> *d_tab;       // FP64 tables
+  bs::OpTab<float> *d_tabf;       // FP32 tables
+  double *d_ApL;                  // [NL] local operator output (FP64 or FP32 view)
+  double *d_vec;                  // 6 x [NG]: r, p, Ap, z, dinv, spare
+  bs::CgState *d_state;
+  double *d_partials;             // [kMaxPartials]
+  unsigned int *d_counter;
+  bs::CgState *h_state;           // pinned host mirror for convergence checks
+  cudaStream_t cap_stream;        // private stream for graph capture
+  cudaGraphExec_t graph;          // cached CG chunk graph
+  const void *graph_key[4];       // (x, hist, flags, chunk) the graph was made for
+};

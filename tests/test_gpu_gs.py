@@ -1,0 +1,88 @@
+"""GPU parity of BS6 (gather) and BS7 (scatter) and of the index maps.
+
+Bitwise against the oracle: the CSR of Z^T (rowStarts, colIds), scatter
+(including masked entries left untouched) and gather (serial sums in
+ascending local order on both sides).  Meshes: structured K^3 hex meshes of
+degree N with seeded element permutations -- the paper's BS6/BS7 workload
+(Sec. 6.2) -- from tiny to several thousand elements, plus masked maps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_10917_gb300 import bs, synth
+
+pytestmark = pytest.mark.gpu
+
+MESHES = [(1, 1), (2, 1), (3, 2), (8, 3), (5, 7), (2, 15), (12, 4)]
+
+
+def masked(m, frac, seed):
+    ids = m.ids.copy()
+    if frac > 0:
+        ids[synth.uniform(ids.size, seed, 0, 0.0, 1.0) < frac] = -1
+    return ids
+
+
+def bits(a):
+    return np.ascontiguousarray(a).view(np.uint64 if a.dtype == np.float64 else np.uint32)
+
+
+@pytest.mark.parametrize("K,N", MESHES)
+@pytest.mark.parametrize("frac", [0.0, 0.07])
+def test_map_scatter_gather(K, N, frac):
+    m = synth.Mesh(K, N, seed=K * 31 + N)
+    ids = masked(m, frac, 5)
+    Z = bs.Map(m.E, N, m.NG, ids)
+    rs, ci = Z.export()
+    ors, oci = oracle.csr(ids, m.NG)
+    assert np.array_equal(rs, ors) and np.array_equal(ci, oci)
+    assert np.array_equal(Z.valence().cpu().numpy(), oracle.valence(ids, m.NG))
+
+    qG = synth.uniform(m.NG, 8)
+    init = np.full(m.NL, -3.5)
+    qL = torch.from_numpy(init).cuda()
+    Z.scatter(torch.from_numpy(qG).cuda(), qL)
+    assert np.array_equal(bits(qL.cpu().numpy()), bits(oracle.scatter(ids, qG, init)))
+
+    ql = synth.uniform(m.NL, 9)
+    g = Z.gather(torch.from_numpy(ql).cuda()).cpu().numpy()
+    assert np.array_equal(bits(g), bits(oracle.gather(ids, ql, m.NG)))
+
+    # FP32 twins
+    qGf = qG.astype(np.float32)
+    qLf = torch.from_numpy(init.astype(np.float32)).cuda()
+    Z.scatter(torch.from_numpy(qGf).cuda(), qLf)
+    assert np.array_equal(bits(qLf.cpu().numpy()),
+                          bits(oracle.scatter_f32(ids, qGf, init.astype(np.float32))))
+    qlf = ql.astype(np.float32)
+    gf = Z.gather(torch.from_numpy(qlf).cuda()).cpu().numpy()
+    assert np.array_equal(bits(gf), bits(oracle.gather_f32(ids, qlf, m.NG)))
+
+
+def test_gather_of_scatter_of_ones_is_valence():
+    m = synth.Mesh(6, 5, seed=3)
+    Z = bs.Map(m.E, m.N, m.NG, m.ids)
+    ones = torch.ones(m.NG, dtype=torch.float64, device="cuda")
+    v = Z.gather(Z.scatter(ones))
+    assert torch.equal(v, Z.valence().to(torch.float64))
+    assert int(Z.valence().sum()) == m.NL
+
+
+def test_unaligned_outputs():
+    m = synth.Mesh(3, 3, seed=2)
+    Z = bs.Map(m.E, m.N, m.NG, m.ids)
+    qG = synth.uniform(m.NG, 1)
+    buf = torch.full((m.NL + 1,), 2.0, dtype=torch.float64, device="cuda")
+    Z.scatter(torch.from_numpy(qG).cuda(), buf[1:])
+    assert np.array_equal(buf[1:].cpu().numpy(), oracle.scatter(m.ids, qG, np.full(m.NL, 2.0)))
+
+
+def test_bad_map_rejected():
+    m = synth.Mesh(2, 2, seed=1)
+    ids = m.ids.copy()
+    ids[5] = m.NG  # out of range
+    with pytest.raises(bs.BSError) as e:
+        bs.Map(m.E, m.N, m.NG, ids)
+    assert e.value.status == bs.BS_ERR_ARG
