@@ -41,7 +41,7 @@ KERNEL_OF = {"copy": "k_copy", "axpy": "k_axpy", "norm": "k_dot", "dot": "k_dot"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--log2n", type=int, default=28, help="vector length 2^k for BS1-BS5")
