@@ -198,6 +198,37 @@ int bs_cg_solve(const bs_problem *prob, const double *b, double *x, double tol,
                 int32_t maxit, int32_t flags, double *d_hist,
                 bs_cg_info *info, void *stream);
 
+/* ------------------------------------------------------------ no allocation */
+
+/* Largest number of per-block partial sums bs_dot_noalloc can hold. */
+#define BS_NOALLOC_MAX_PARTIALS 2048
+
+/* bs_dot_noalloc: the inner product x.y of bs_dot, written to d_out[0]
+ * (DEVICE), for callers that must not allocate device memory -- code running
+ * inside a host application that owns every device allocation through its
+ * own pool, or a latency-critical loop where the implicit device
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.  The paper has
+ * no counterpart to this entry point.
+ *
+ * Instead of a bs_workspace it uses scratch compiled into the library: a
+ * static device array of BS_NOALLOC_MAX_PARTIALS doubles plus an arrival
+ * counter (about 16 KiB), present on every GPU that loads libbs and held
+ * until the process exits.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine); the caller passes the inputs and
+ * the output.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make
+ *    that first call before any stream capture begins.
+ *  - Every call shares the one array, which keeps the previous call's
+ *    contents; the counter is cleared on `stream` at the start of each call.
+ *    Calls that overlap on the GPU (on different streams, or from several
+ *    threads) race on the array and give wrong results: serialise them.
+ *  - Returns BS_ERR_ARG if the launch would need more than
+ *    BS_NOALLOC_MAX_PARTIALS partials (a device with more resident blocks
+ *    than that), or on the argument errors of bs_dot. */
+int bs_dot_noalloc(int64_t n, const double *x, const double *y, double *d_out,
+                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif
