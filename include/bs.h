@@ -198,6 +198,24 @@ int bs_cg_solve(const bs_problem *prob, const double *b, double *x, double tol,
                 int32_t maxit, int32_t flags, double *d_hist,
                 bs_cg_info *info, void *stream);
 
+/* CG with FP32 vectors inside FP64 iterative refinement (the mixed-precision
+ * form of Algorithm 1; no counterpart in the paper, which studies FP64 only).
+ * Outer loop in FP64: r = b - A x; stop when ||r|| <= tol ||b|| (the FP64
+ * TRUE residual); else solve A d = r by Algorithm 1 with every vector and the
+ * operator in FP32 (dot products carried as float pairs, alpha and beta in
+ * double) to ||r_d|| <= inner_tol ||r||, then x = x + d in FP64.
+ * maxit caps the total inner iterations, outer_maxit the refinement steps.
+ * flags: BS_CG_GRAPH (inner iterations replayed as a CUDA graph), BS_CG_X0.
+ * info->iterations = inner iterations, info->outer = refinement steps,
+ * info->rel_residual = ||b - A x|| / ||b|| in FP64.  Synchronises `stream`.
+ * The problem owns the FP32 scratch (four N_G float vectors, allocated on
+ * the first call).  Returns BS_ERR_NOT_CONVERGED or BS_ERR_BREAKDOWN as
+ * bs_cg_solve does. */
+int bs_cg_solve_refined_f32(const bs_problem *prob, const double *b, double *x,
+                            double tol, int32_t maxit, double inner_tol,
+                            int32_t outer_maxit, int32_t flags, bs_cg_info *info,
+                            void *stream);
+
 /* ------------------------------------------------------------ no allocation */
 
 /* Largest number of per-block partial sums bs_dot_noalloc can hold. */

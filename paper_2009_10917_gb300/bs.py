@@ -90,6 +90,8 @@ _SIGS = {
     "bs_diag_A": (ctypes.c_int, [_vp, _vp, _vp]),
     "bs_cg_solve": (ctypes.c_int, [_vp, _vp, _vp, _d, _i32, _i32, _vp,
                                    ctypes.POINTER(CgInfo), _vp]),
+    "bs_cg_solve_refined_f32": (ctypes.c_int, [_vp, _vp, _vp, _d, _i32, _d, _i32, _i32,
+                                               ctypes.POINTER(CgInfo), _vp]),
 }
 
 
@@ -319,6 +321,21 @@ class Problem:
                                _stream())
         if check and rc not in (BS_OK,):
             _check(rc, "bs_cg_solve")
+        d = info.as_dict()
+        d["rc"] = rc
+        return x, d
+
+    def cg_refined_f32(self, b, x=None, tol=1e-10, maxit=100000, inner_tol=1e-4,
+                       outer_maxit=50, flags=0, check=True):
+        """FP32 CG inside FP64 iterative refinement.  Returns (x, info dict);
+        info['rel_residual'] is the FP64 true relative residual."""
+        if x is None:
+            x = torch.zeros_like(b)
+        info = CgInfo()
+        rc = lib().bs_cg_solve_refined_f32(self.handle, _ptr(b), _ptr(x), tol, maxit, inner_tol,
+                                           outer_maxit, flags, ctypes.byref(info), _stream())
+        if check and rc != BS_OK:
+            _check(rc, "bs_cg_solve_refined_f32")
         d = info.as_dict()
         d["rc"] = rc
         return x, d

@@ -167,8 +167,8 @@ static int cg_iteration(const bs_problem *P, double *x, bool precond, cudaStream
   CgVecs v = vecs(P);
   CgState *st = P->d_state;
   const double g = 0.5 * P->h, mlam = P->lambda * g * g * g;
-  int rc = launch_ax_local<double, true>(P->N, m->E, m->d_ids, v.p, P->d_ApL, P->d_tab,
-                                         P->d_coef, g, mlam, st, s);
+  int rc = launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, P->d_ApL,
+                                         P->d_tab, P->d_coef, g, mlam, st, s);
   if (rc) return rc;
   rc = launch_gather<double, true, EpAlpha>(m, P->d_ApL, v.Ap, v.p, P->d_partials, P->d_counter,
                                             EpAlpha{st, precond ? 1 : 0}, st, s);

@@ -1,7 +1,10 @@
 // bs_gs.cu -- the scatter operator Z (eq. scatter_def) as a map object, and
 // the C ABI entry points of BS6 (gather) and BS7 (scatter).
+#include <algorithm>
+#include <climits>
 #include <cstdlib>
 #include <cstring>
+#include <numeric>
 #include <vector>
 
 #include "bs_gs.cuh"
@@ -28,6 +31,8 @@ static void free_map(bs_map *m) {
   cudaFree(m->d_ids);
   cudaFree(m->d_row_starts);
   cudaFree(m->d_col_ids);
+  cudaFree(m->d_tiles);
+  cudaFree(m->d_elem_order);
   free(m);
 }
 
@@ -83,6 +88,35 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
       if (id >= 0) col[(size_t)fill[(size_t)id]++] = (int32_t)l;
     }
   }
+  // gather tiles: at most kTileRows consecutive rows holding at most kTileNnz
+  // CSR entries (a longer row gets a tile of its own); at least one tile
+  std::vector<int32_t> tiles;
+  tiles.push_back(0);
+  for (int64_t g = 0; g < NG;) {
+    int64_t r = g;
+    while (r < NG && r - g < kTileRows && rs[(size_t)r + 1] - rs[(size_t)g] <= kTileNnz) ++r;
+    if (r == g) r = g + 1;
+    tiles.push_back((int32_t)r);
+    g = r;
+  }
+  if (tiles.size() == 1) tiles.push_back(0);
+  std::vector<int2> tile_bounds(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i)
+    tile_bounds[i] = make_int2(tiles[i], rs[(size_t)tiles[i]]);
+  // elements in the order of their smallest global index (ties keep storage
+  // order); all-masked elements go last
+  std::vector<int32_t> order((size_t)E);
+  {
+    std::vector<int32_t> key((size_t)E, INT32_MAX);
+    for (int64_t l = 0; l < NL; ++l) {
+      const int32_t id = h_l2g[l];
+      int32_t &k = key[(size_t)(l / Np)];
+      if (id >= 0 && id < k) k = id;
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return key[(size_t)a] < key[(size_t)b]; });
+  }
   bs_map *m = (bs_map *)calloc(1, sizeof(bs_map));
   if (!m) return fail(BS_ERR_ALLOC, "bs_map_create: host allocation");
   m->E = E;
@@ -90,6 +124,7 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
   m->NL = NL;
   m->NG = NG;
   m->nnz = nnz;
+  m->ntiles = (int64_t)tiles.size() - 1;
   cudaError_t e = cudaGetDevice(&m->device);
   // +4 elements of padding so 128-bit loads of the map never leave the buffer
   if (e == cudaSuccess) e = cudaMalloc(&m->d_ids, sizeof(int32_t) * (NL + 4));
@@ -102,6 +137,13 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nnz)
     e = cudaMemcpy(m->d_col_ids, col.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_tiles, sizeof(int2) * tile_bounds.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_tiles, tile_bounds.data(), sizeof(int2) * tile_bounds.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_elem_order, sizeof(int32_t) * (E > 0 ? E : 1));
+  if (e == cudaSuccess && E)
+    e = cudaMemcpy(m->d_elem_order, order.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_map(m);
     return fail(BS_ERR_CUDA, "bs_map_create: %s", cudaGetErrorString(e));

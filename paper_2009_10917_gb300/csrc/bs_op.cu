@@ -125,6 +125,7 @@ static void free_problem(bs_problem *p) {
   cudaFree(p->d_vec);
   cudaFree(p->d_state);
   cudaFree(p->d_partials);
+  cudaFree(p->d_f32);
   if (p->h_state) cudaFreeHost(p->h_state);
   free(p);
 }
@@ -203,8 +204,8 @@ int bs_apply_local(const bs_problem *p, const double *uL, double *AuL, void *str
   if (p->map->NL == 0) return BS_OK;
   BS_ARG(uL && AuL, "bs_apply_local: NULL vector");
   const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
-  return launch_ax_local<double, false>(p->N, p->map->E, nullptr, uL, AuL, p->d_tab, p->d_coef,
-                                        g, mlam, nullptr, as_stream(stream));
+  return launch_ax_local<double, false>(p->N, p->map->E, nullptr, nullptr, uL, AuL, p->d_tab,
+                                        p->d_coef, g, mlam, nullptr, as_stream(stream));
 }
 
 int bs_apply_A(const bs_problem *p, const double *x, double *Ax, void *stream) {
@@ -213,8 +214,9 @@ int bs_apply_A(const bs_problem *p, const double *x, double *Ax, void *stream) {
   BS_ARG(x && Ax, "bs_apply_A: NULL vector");
   const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
   cudaStream_t s = as_stream(stream);
-  if (int rc = launch_ax_local<double, true>(p->N, p->map->E, p->map->d_ids, x, p->d_ApL,
-                                             p->d_tab, p->d_coef, g, mlam, nullptr, s))
+  if (int rc = launch_ax_local<double, true>(p->N, p->map->E, p->map->d_elem_order,
+                                             p->map->d_ids, x, p->d_ApL, p->d_tab, p->d_coef, g,
+                                             mlam, nullptr, s))
     return rc;
   return launch_gather<double, false, EpNone>(p->map, p->d_ApL, Ax, nullptr, nullptr, nullptr,
                                               EpNone{}, nullptr, s);

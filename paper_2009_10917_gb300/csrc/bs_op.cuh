@@ -38,11 +38,13 @@ struct OpShape {
 
 // out = A_L in  on E elements.  GATHER_IN: in is a global vector read
 // through ids (masked nodes read as 0); else in is element-local.
-// g = c-independent stiffness factor h/2, mlam = lambda (h/2)^3.
+// g = c-independent stiffness factor h/2, mlam = lambda (h/2)^3.  Elements
+// are visited in `order` (elements sorted by smallest global index, so the
+// indexed reads of neighbouring elements meet in L2) when it is given.
 template <typename T, int NQ, bool GATHER_IN>
 __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
-    k_ax_local(int64_t E, const int32_t *__restrict__ ids, const T *__restrict__ in,
-               T *__restrict__ out, const OpTab<T> *__restrict__ tab,
+    k_ax_local(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
+               const T *__restrict__ in, T *__restrict__ out, const OpTab<T> *__restrict__ tab,
                const double *__restrict__ coef, T g, T mlam, const CgState *st) {
   using S = OpShape<NQ>;
   __shared__ T s_u[S::EPB][S::NP];
@@ -54,8 +56,9 @@ __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
   const int le = threadIdx.x / S::NQ2;
   const int ij = threadIdx.x - le * S::NQ2;
   const int i = ij % NQ, j = ij / NQ;
-  const int64_t e = (int64_t)blockIdx.x * S::EPB + le;
-  const bool active = le < S::EPB && e < E;
+  const int64_t slot = (int64_t)blockIdx.x * S::EPB + le;
+  const bool active = le < S::EPB && slot < E;
+  const int64_t e = active && order ? (int64_t)order[slot] : slot;
   T ureg[NQ];
   if (active) {
     const int64_t base = e * S::NP + ij;
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
 }
 
 template <typename T, bool GATHER_IN>
-int launch_ax_local(int N, int64_t E, const int32_t *ids, const T *in, T *out,
+int launch_ax_local(int N, int64_t E, const int32_t *order, const int32_t *ids, const T *in,
+                    T *out,
                     const OpTab<T> *tab, const double *coef, T g, T mlam,
                     const CgState *st, cudaStream_t s) {
   if (E == 0) return BS_OK;
@@ -106,9 +110,8 @@ int launch_ax_local(int N, int64_t E, const int32_t *ids, const T *in, T *out,
   case NQ: {                                                                             \
     using Sh = OpShape<NQ>;                                                              \
     const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                    \
-    k_ax_local<T, NQ, GATHER_IN><<<(unsigned)grid, Sh::THREADS, 0, s>>>(E, ids, in, out, \
-                                                                       tab, coef, g,    \
-                                                                       mlam, st);       \
+    k_ax_local<T, NQ, GATHER_IN><<<(unsigned)grid, Sh::THREADS, 0, s>>>(                 \
+        E, order, ids, in, out, tab, coef, g, mlam, st);                                 \
     break;                                                                               \
   }
   switch (N + 1) {
@@ -154,5 +157,6 @@ struct bs_problem {
   bs::CgState *h_state;           // pinned host mirror for convergence checks
   cudaStream_t cap_stream;        // private stream for graph capture
   cudaGraphExec_t graph;          // cached CG chunk graph
-  const void *graph_key[4];       // (x, hist, flags, chunk) the graph was made for
+  const void *graph_key[4];       // (x, variant, chunk, map) the graph was made for
+  float *d_f32;                   // 4 x [NG + 8] FP32 vectors (refined solver), lazily
 };

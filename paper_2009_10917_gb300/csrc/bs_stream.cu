@@ -76,7 +76,11 @@ int bs_axpy_f32(int64_t n, float alpha, const float *x, float beta, float *y, vo
 }
 
 int bs_norm(int64_t n, const double *x, double *d_out, bs_workspace *ws, void *stream) {
-  return do_dot<double, true>(n, x, x, EpNorm{d_out}, d_out, ws, stream, "bs_norm");
+  BS_ARG(n >= 0, "bs_norm: n < 0");
+  BS_ARG(d_out != nullptr, "bs_norm: NULL output");
+  if (int rc = check_ws(ws, "bs_norm")) return rc;
+  if (n > 0) BS_ARG(x != nullptr, "bs_norm: NULL vector");
+  return launch_norm_split(n, x, ws->partials, ws->counter, EpNorm{d_out}, as_stream(stream));
 }
 int bs_norm_f32(int64_t n, const float *x, double *d_out, bs_workspace *ws, void *stream) {
   return do_dot<float, true>(n, x, x, EpNorm{d_out}, d_out, ws, stream, "bs_norm_f32");

@@ -316,6 +316,123 @@ int launch_dot(int64_t n, const T *x, const T *y, double *partials, unsigned int
   return BS_OK;
 }
 
+// ------------------------------------------------------------ BS3 norm, FP64
+
+// On GB300 one DFMA per 8 bytes read is more than the FP64 pipe sustains, so
+// the FP64 norm moves half of the squares onto the FP32 pipes.  An element x
+// with 2^-30 <= |x| < 2^31 is split exactly by integer operations into
+// h = x truncated to 24 significant bits (a float) and l = the remaining 29
+// bits rounded to a float (relative error of h + l below 2^-47); then
+// x^2 = h^2 + (fma(h, h, -h^2) + 2 h l + l^2), the first term exact.  These
+// pairs accumulate as an unevaluated float pair for 16 elements, then the
+// chunk joins a double accumulator.  Every other element (and any element
+// outside the window: zeros, subnormals, huge values) takes a DFMA.
+struct SqAcc {
+  FF f{0.f, 0.f};
+  double d = 0.0;    // FP64 squares and flushed float-pair chunks
+  double dd = 0.0;   // second FP64 chain for ILP
+  __device__ __forceinline__ void add_dfma(double x) { dd = fma(x, x, dd); }
+  __device__ __forceinline__ void add_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned E = (hw >> 20) & 0x7ffu;
+    if (E - 993u > 60u) {  // outside [2^-30, 2^31)
+      d = fma(x, x, d);
+      return;
+    }
+    const unsigned sign = hw & 0x80000000u;
+    const float h = __uint_as_float(sign | ((E - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    // l = the low 29 bits r, rounded to a multiple of 2^6, times 2^(E - 1075):
+    // with base = 2^(E - 1046) as a float, the bit pattern base + rr is
+    // base * (1 + rr / 2^23), so subtracting base leaves rr * 2^(E - 1069)
+    // exactly (rr = 2^23 carries into the exponent and still gives rr * 2^..).
+    // Integer and FP32 operations only: conversion instructions share GB300's
+    // narrow FP64 pipe.
+    const unsigned rr = ((lw & 0x1fffffffu) + 32u) >> 6;
+    const unsigned base = (E - 919u) << 23;
+    const float l = __uint_as_float(
+        __float_as_uint(__uint_as_float(base + rr) - __uint_as_float(base)) | sign);
+    const float p = h * h;
+    const float t = fmaf(h + h, l, fmaf(l, l, fmaf(h, h, -p)));
+    const float s = f.hi + p;  // TwoSum(f.hi, p)
+    const float bp = s - f.hi;
+    const float err = (f.hi - (s - bp)) + (p - bp);
+    f.hi = s;
+    f.lo = f.lo + (err + t);
+  }
+  // A normal or zero float as a double, by assembling the bits (no
+  // conversion instruction).  Subnormal floats (never produced here: the
+  // window keeps every term above 2^-120) would flush to zero.
+  static __device__ __forceinline__ double widen(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  __device__ __forceinline__ void flush() {
+    d = d + (widen(f.hi) + widen(f.lo));
+    f.hi = 0.f;
+    f.lo = 0.f;
+  }
+  __device__ __forceinline__ double value() {
+    flush();
+    return d + dd;
+  }
+};
+
+template <int U, class Ep>
+__global__ void __launch_bounds__(kReduceBlock)
+    k_norm_split(Split sp, const double *__restrict__ x, double *partials, unsigned int *counter,
+                 Ep ep) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const double2 *xv = reinterpret_cast<const double2 *>(x + sp.head);
+  SqAcc acc;
+  int64_t i = tid;
+  int chunk = 0;
+  for (; i + (U - 1) * nth < sp.nvec; i += U * nth) {
+    double2 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = ld_stream(xv + i + u * nth);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      acc.add_split(a[u].x);
+      acc.add_dfma(a[u].y);
+    }
+    if (++chunk == 16 / U) {
+      acc.flush();
+      chunk = 0;
+    }
+  }
+  for (; i < sp.nvec; i += nth) {
+    const double2 a = ld_stream(xv + i);
+    acc.add_dfma(a.x);
+    acc.add_dfma(a.y);
+  }
+  for (int64_t j = tid; j < sp.head; j += nth) acc.add_dfma(x[j]);
+  for (int64_t j = sp.tail0 + tid; j < sp.n; j += nth) acc.add_dfma(x[j]);
+  const double part = block_sum<kReduceBlock>(acc.value());
+  double total;
+  if (grid_combine<kReduceBlock>(part, partials, counter, &total) && threadIdx.x == 0) ep(total);
+}
+
+template <class Ep>
+int launch_norm_split(int64_t n, const double *x, double *partials, unsigned int *counter, Ep ep,
+                      cudaStream_t s) {
+  constexpr int U = 4;
+  const void *ptrs[1] = {x};
+  Split sp = make_split<double>(n, ptrs, 1);
+  auto kern = k_norm_split<U, Ep>;
+  const int64_t work = sp.nvec > 0 ? sp.nvec : n;
+  int grid = stream_grid(work, U, kReduceBlock, blocks_per_sm(kern, kReduceBlock));
+  if (grid < 1) return fail(BS_ERR_CUDA, "no device");
+  if (grid > kMaxPartials) grid = kMaxPartials;
+  kern<<<grid, kReduceBlock, 0, s>>>(sp, x, partials, counter, ep);
+  BS_LAUNCH_CHECK();
+  return BS_OK;
+}
+
 // ------------------------------------------------------------ BS5 fused CG update
 
 // x = fma(alpha, p, x); r = fma(-alpha, Ap, r); total = sum r^2; one pass.

@@ -86,3 +86,30 @@ def test_bad_map_rejected():
     with pytest.raises(bs.BSError) as e:
         bs.Map(m.E, m.N, m.NG, ids)
     assert e.value.status == bs.BS_ERR_ARG
+
+
+def test_gather_row_longer_than_a_tile():
+    """A global node with more local copies than one gather tile stages (2048)
+    takes the direct path; the sum order stays ascending."""
+    m = synth.Mesh(3, 4, seed=1)
+    ids = m.ids.copy()
+    ids[:2500] = 0           # one row of 2500 entries
+    ids[3000:3100] = 7       # and a long-but-fitting one
+    Z = bs.Map(m.E, m.N, m.NG, ids)
+    ql = synth.uniform(m.NL, 4)
+    g = Z.gather(torch.from_numpy(ql).cuda()).cpu().numpy()
+    assert np.array_equal(bits(g), bits(oracle.gather(ids, ql, m.NG)))
+    rs, ci = Z.export()
+    ors, oci = oracle.csr(ids, m.NG)
+    assert np.array_equal(rs, ors) and np.array_equal(ci, oci)
+
+
+def test_gather_negative_zero_sums():
+    """Sums start from +0.0: a single -0.0 copy gathers to +0.0, as in the
+    definition; -0.0 + -0.0 from +0.0 is +0.0 too."""
+    m = synth.Mesh(2, 2, seed=1)
+    Z = bs.Map(m.E, m.N, m.NG, m.ids)
+    ql = np.full(m.NL, -0.0)
+    g = Z.gather(torch.from_numpy(ql).cuda()).cpu().numpy()
+    assert np.array_equal(bits(g), bits(oracle.gather(m.ids, ql, m.NG)))
+    assert np.all(bits(g) == 0)

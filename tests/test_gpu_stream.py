@@ -140,3 +140,24 @@ def test_argument_errors():
     with pytest.raises(bs.BSError) as e:
         bs.axpy(1.0, x, 1.0, x)  # aliasing is rejected
     assert e.value.status == bs.BS_ERR_ARG
+
+
+@pytest.mark.parametrize("n", [1001, 1 << 20])
+def test_norm_values_outside_the_float_pair_window(n):
+    """The FP64 norm squares elements with 2^-30 <= |x| < 2^31 as float pairs and
+    everything else (zeros, subnormals, tiny and huge values) with DFMA."""
+    x = synth.uniform(n, 9)
+    sel = synth.uniform(n, 9, 1, 0.0, 1.0)
+    x = np.where(sel < 0.1, x * 1e-12, x)
+    x = np.where((sel >= 0.1) & (sel < 0.2), x * 1e12, x)
+    x = np.where((sel >= 0.2) & (sel < 0.25), 0.0, x)
+    x = np.where((sel >= 0.25) & (sel < 0.27), 5e-320, x)
+    x = np.where((sel >= 0.27) & (sel < 0.3), x * 2.0 ** 31, x)
+    x = np.where((sel >= 0.3) & (sel < 0.33), x * 2.0 ** -30, x)
+    nr = host(bs.norm(dev(x)))
+    s, sq = oracle.norm(x)
+    assert rel(nr[0], s) <= 1e-13 and rel(nr[1], sq) <= 1e-13
+    # small magnitudes only: the result must not be lost to the large terms
+    y = synth.uniform(n, 10) * 2.0 ** -29
+    nr = host(bs.norm(dev(y)))
+    assert rel(nr[0], oracle.norm(y)[0]) <= 1e-13
