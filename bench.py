@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--mesh", default="7,48", help="N,K of the BS6/BS7 mesh")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-tolerance runs")
+    ap.add_argument("--workload", default="stream", choices=["stream", "cg"],
+                    help="stream: the BS step (default); cg: only the CG solves on --cg-mesh")
+    ap.add_argument("--cg-mesh", default="7,48", help="N,K of the CG time-to-tolerance mesh")
+    ap.add_argument("--no-cg-small", action="store_true", help="skip the N=3, 8^3 CG runs")
     return ap.parse_args()
 
 
@@ -271,6 +276,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args)
+    cg = None
+    if not args.no_cg:
+        del dev, y, qL, qG2
+        torch.cuda.empty_cache()
+        cg = cg_section(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -279,10 +289,56 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config(args, n, mesh.N, mesh.K, NL, NG),
                 "per_op": per_op, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 7 * args.steps, "clocks": clk.summary()}
+                "gpu_launches": 7 * args.steps, "clocks": clk.summary(), "cg": cg}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def cg_section(args):
+    """Time to tolerance of Algorithm 1 on the GLL Helmholtz operator
+    (lambda = 1, b uniform[-1, 1)): plain FP64 CG to 1e-8, and FP32-storage CG
+    inside FP64 iterative refinement to 1e-8 and 1e-10 (FP64 true residual),
+    each after one untimed warm-up solve; plus the small configuration's 50
+    fixed FP64 iterations.  Wall time measured by the library around each
+    solve (host clock, stream synchronised)."""
+    import torch
+
+    from paper_2009_10917_gb300 import bs, synth
+    out = {}
+    N, K = (int(v) for v in args.cg_mesh.split(","))
+    cases = [] if args.no_cg_small else [("small_N3_K8", (3, 8))]
+    for label, (n_, k_) in cases + [(f"N{N}_K{K}", (N, K))]:
+        m = synth.Mesh(k_, n_, seed=1)
+        Z = bs.Map(m.E, n_, m.NG, m.ids)
+        P = bs.Problem(Z, m.h, 1.0)
+        b = torch.from_numpy(synth.uniform(m.NG, 1, stream=7)).cuda()
+        res = {"N_G": m.NG, "N_L": m.NL}
+        if label.startswith("small"):
+            P.cg(b, tol=0.0, maxit=50, flags=bs.BS_CG_FIXED_ITERS | bs.BS_CG_GRAPH)
+            _, i50 = P.cg(b, tol=0.0, maxit=50, flags=bs.BS_CG_FIXED_ITERS | bs.BS_CG_GRAPH)
+            res["fp64_50_iterations_s"] = i50["seconds"]
+        runs = [("fp64_cg", lambda: P.cg(b, tol=1e-8, maxit=100000, flags=bs.BS_CG_GRAPH)),
+                ("fp32_ir_1e-8", lambda: P.cg_refined_f32(b, tol=1e-8, flags=bs.BS_CG_GRAPH)),
+                ("fp32_ir_1e-10", lambda: P.cg_refined_f32(b, tol=1e-10, flags=bs.BS_CG_GRAPH))]
+        for name, fn in runs:
+            fn()
+            _, info = fn()
+            res[name] = {"seconds": round(info["seconds"], 4), "iterations": info["iterations"],
+                         "outer": info["outer"], "rel_residual": info["rel_residual"]}
+        res["speedup_fp32_ir_vs_fp64_at_1e-8"] = round(
+            res["fp64_cg"]["seconds"] / res["fp32_ir_1e-8"]["seconds"], 3)
+        out[label] = res
+        del P, Z, b
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_cg_only(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps({"metric": "time-to-1e-8 CG solve, plain vs FP32-refined", "unit": "s",
+                      "higher_is_better": False, "cg": cg_section(args)}), flush=True)
 
 
 def traffic_for(kernel, op):
@@ -370,5 +426,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "cg":
+        run_cg_only(a)
     else:
         run_ours(a)

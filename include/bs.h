@@ -203,7 +203,7 @@ int bs_cg_solve(const bs_problem *prob, const double *b, double *x, double tol,
  * Outer loop in FP64: r = b - A x; stop when ||r|| <= tol ||b|| (the FP64
  * TRUE residual); else solve A d = r by Algorithm 1 with every vector and the
  * operator in FP32 (dot products carried as float pairs, alpha and beta in
- * double) to ||r_d|| <= inner_tol ||r||, then x = x + d in FP64.
+ * double) to ||r_d|| <= inner_tol ||r|| from d_0 = 0, then x = x + d in FP64.
  * maxit caps the total inner iterations, outer_maxit the refinement steps.
  * flags: BS_CG_GRAPH (inner iterations replayed as a CUDA graph), BS_CG_X0.
  * info->iterations = inner iterations, info->outer = refinement steps,

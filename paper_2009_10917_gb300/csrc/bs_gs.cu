@@ -7,7 +7,7 @@
 #include <numeric>
 #include <vector>
 
-#include "bs_gs.cuh"
+#include "bs_gather.cuh"
 
 namespace bs {
 

@@ -15,7 +15,7 @@
 // scatter Z p into the same pass, so the N_L-sized Z p is never stored.
 #pragma once
 
-#include "bs_gs.cuh"
+#include "bs_gather.cuh"
 
 namespace bs {
 

@@ -7,10 +7,13 @@
 // the same four kernels per iteration as the FP64 solver (fused scatter +
 // element operator, gather with p.Ap, fused update with r.r, AXPY), their
 // reductions carried as float pairs and combined in double, alpha and beta
-// formed in double and rounded to float for the updates.  The inner solve
+// formed in double and rounded to float for the updates.  Each inner solve
 // stops at ||r_d|| <= inner_tol ||r||.  Halving the bytes of every vector and
 // moving the element operator from GB300's narrow FP64 pipe to the FP32
 // pipes is what makes this faster than the FP64 solve at equal accuracy.
+// Every inner solve starts afresh (d_0 = 0, p = r): keeping the search
+// direction across a residual replacement was tried and stalled on
+// ill-conditioned cases without saving iterations where it converged.
 #include <chrono>
 #include <cmath>
 #include <cstring>

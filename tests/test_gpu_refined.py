@@ -35,10 +35,10 @@ def test_refined_reaches_fp64_tolerance(K, N, lam, with_coef, graph):
     assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b)
     xo, it, *_ = oracle.cg(m.E, N, m.h, lam, m.ids, m.NG, b, tol=1e-12, maxit=20000, coef=coef)
     assert np.linalg.norm(xg - xo) <= 1e3 * 1e-10 * np.linalg.norm(xo)
+    assert info["outer"] >= 2  # FP32 alone cannot reach 1e-10
     _, inner, outer, rel = oracle.cg_ir_f32(m.E, N, m.h, lam, m.ids, m.NG, b, 1e-10, coef=coef)
     assert rel <= 1e-10
     assert abs(info["outer"] - outer) <= 1
-    assert info["outer"] >= 2  # FP32 alone cannot reach 1e-10
 
 
 def test_refined_initial_guess_and_zero_rhs():
