@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-tolerance runs")
-    ap.add_argument("--workload", default="stream", choices=["stream", "cg"],
-                    help="stream: the BS step (default); cg: only the CG solves on --cg-mesh")
+    ap.add_argument("--workload", default="stream", choices=["stream", "cg", "batched"],
+                    help="stream: the BS step (default); cg: only the CG solves on --cg-mesh; "
+                         "batched: 256 uneven solves, batched vs one at a time")
+    ap.add_argument("--nsolves", type=int, default=256, help="solves in the batched workload")
     ap.add_argument("--cg-mesh", default="7,48", help="N,K of the CG time-to-tolerance mesh")
     ap.add_argument("--no-cg-small", action="store_true", help="skip the N=3, 8^3 CG runs")
     return ap.parse_args()
@@ -319,8 +321,7 @@ def cg_section(args):
             _, i50 = P.cg(b, tol=0.0, maxit=50, flags=bs.BS_CG_FIXED_ITERS | bs.BS_CG_GRAPH)
             res["fp64_50_iterations_s"] = i50["seconds"]
         runs = [("fp64_cg", lambda: P.cg(b, tol=1e-8, maxit=100000, flags=bs.BS_CG_GRAPH)),
-                ("fp32_ir_1e-8", lambda: P.cg_refined_f32(b, tol=1e-8, flags=bs.BS_CG_GRAPH)),
-                ("fp32_ir_1e-10", lambda: P.cg_refined_f32(b, tol=1e-10, flags=bs.BS_CG_GRAPH))]
+                ("fp32_ir_1e-8", lambda: P.cg_refined_f32(b, tol=1e-8, flags=bs.BS_CG_GRAPH))]
         for name, fn in runs:
             fn()
             _, info = fn()
@@ -331,6 +332,64 @@ def cg_section(args):
         out[label] = res
         del P, Z, b
         torch.cuda.empty_cache()
+    return out
+
+
+def batched_section(args):
+    """The batched configuration: nsolves independent solves, degree N uniform
+    in {2..8}, K uniform in {4..24} (seed 7), lambda = 1, b uniform[-1, 1),
+    tol 1e-8.  Times the batched solver (FP64 and FP32-refined, CUDA graph)
+    and the same solves one at a time (FP64 CG and FP32-IR), each after one
+    untimed warm-up pass."""
+    import time
+
+    import torch
+
+    from paper_2009_10917_gb300 import bs, synth
+    specs = synth.batched_specs(args.nsolves, 7)
+    probs, bs_ = [], []
+    keep = []
+    for i, (N, K) in enumerate(specs):
+        m = synth.Mesh(K, N, seed=1000 + i)
+        Z = bs.Map(m.E, N, m.NG, m.ids)
+        P = bs.Problem(Z, m.h, 1.0)
+        keep.append(Z)
+        probs.append(P)
+        bs_.append(torch.from_numpy(synth.uniform(m.NG, 1000 + i, stream=3)).cuda())
+    xs = [torch.zeros_like(b) for b in bs_]
+    out = {"nsolves": len(specs), "sum_N_G": int(sum((k * n + 1) ** 3 for n, k in specs))}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    for name, flags in (("batched_fp64", bs.BS_CG_GRAPH),
+                        ("batched_fp32_ir", bs.BS_CG_GRAPH | bs.BS_CG_REFINED_F32)):
+        dt, (rc, infos) = timed(lambda: bs.solve_batched(probs, bs_, xs, tol=1e-8, flags=flags,
+                                                         check=False))
+        out[name] = {"seconds": round(dt, 3), "rc": rc,
+                     "max_rel_residual": max(i["rel_residual"] for i in infos),
+                     "iterations_sum": sum(i["iterations"] for i in infos)}
+
+    def one_by_one(refined):
+        worst = 0.0
+        for P, b in zip(probs, bs_):
+            if refined:
+                _, info = P.cg_refined_f32(b, tol=1e-8, flags=bs.BS_CG_GRAPH, check=False)
+            else:
+                _, info = P.cg(b, tol=1e-8, maxit=100000, flags=bs.BS_CG_GRAPH, check=False)
+            worst = max(worst, info["rel_residual"])
+        return worst
+
+    for name, refined in (("sequential_fp64", False), ("sequential_fp32_ir", True)):
+        dt, worst = timed(lambda: one_by_one(refined))
+        out[name] = {"seconds": round(dt, 3), "max_rel_residual": worst}
+    out["speedup_batched_fp32_ir_vs_sequential_fp64"] = round(
+        out["sequential_fp64"]["seconds"] / out["batched_fp32_ir"]["seconds"], 3)
     return out
 
 
@@ -428,5 +487,11 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "cg":
         run_cg_only(a)
+    elif a.workload == "batched":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"metric": "time-to-1e-8 CG solve, batched vs one at a time",
+                          "unit": "s", "higher_is_better": False,
+                          "batched": batched_section(a)}), flush=True)
     else:
         run_ours(a)

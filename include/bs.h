@@ -173,7 +173,8 @@ enum {
   BS_CG_FIXED_ITERS = 1, /* run exactly maxit iterations                   */
   BS_CG_JACOBI = 2,      /* Jacobi preconditioner z = diag(A)^-1 r         */
   BS_CG_GRAPH = 4,       /* replay the iteration as a captured CUDA graph  */
-  BS_CG_X0 = 8           /* x holds the initial guess (else x0 = 0)        */
+  BS_CG_X0 = 8,          /* x holds the initial guess (else x0 = 0)        */
+  BS_CG_REFINED_F32 = 32 /* batched: FP32 inner CG, FP64 refinement        */
 };
 
 typedef struct {
@@ -215,6 +216,32 @@ int bs_cg_solve_refined_f32(const bs_problem *prob, const double *b, double *x,
                             double tol, int32_t maxit, double inner_tol,
                             int32_t outer_maxit, int32_t flags, bs_cg_info *info,
                             void *stream);
+
+/* bs_cg_solve_batched: nsolves independent solves A_s x_s = b_s (Algorithm 1
+ * on each; no counterpart in the paper, which runs one problem at a time),
+ * advanced together.  Each CG iteration of all still-running solves is ONE
+ * cooperative launch: fused scatter + element operator, gather with p.Ap,
+ * fused update with r.r and the search-direction update, separated by grid
+ * barriers; alpha, beta and the stop flag of every solve are formed on the
+ * device from per-item partial sums taken in a fixed order (deterministic).
+ * Solves that have stopped drop out of the work lists at no cost.
+ *  - probs[s] must be distinct problems on the current device (each lends its
+ *    scratch); b[s], x[s] are DEVICE vectors of its N_G; x0 = 0.
+ *  - Stop: r.r <= tol^2 b.b per solve, or maxit iterations.
+ *  - flags: BS_CG_GRAPH (iterations replayed as a CUDA graph),
+ *    BS_CG_REFINED_F32 (FP32-storage inner CG of every solve inside an FP64
+ *    iterative refinement done for all solves together; inner tolerance 1e-4,
+ *    at most 50 refinement steps; then tol is met by the FP64 TRUE residual
+ *    and maxit caps each solve's total inner iterations).
+ *  - infos[s] (host, may be NULL) receives each solve's iterations, outer
+ *    steps, final r.r, b.b, relative residual, status; seconds is the whole
+ *    batch's wall time.  Synchronises `stream`.
+ *  - Grid barrier waits are bounded (about 2 s); on expiry the call returns
+ *    BS_ERR_TIMEOUT.  Returns the first failing solve's status otherwise. */
+int bs_cg_solve_batched(int32_t nsolves, const bs_problem *const *probs,
+                        const double *const *b, double *const *x, double tol,
+                        int32_t maxit, int32_t flags, bs_cg_info *infos,
+                        void *stream);
 
 /* ------------------------------------------------------------ no allocation */
 

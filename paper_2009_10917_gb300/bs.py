@@ -32,6 +32,7 @@ BS_CG_FIXED_ITERS = 1
 BS_CG_JACOBI = 2
 BS_CG_GRAPH = 4
 BS_CG_X0 = 8
+BS_CG_REFINED_F32 = 32
 
 
 class BSError(RuntimeError):
@@ -92,6 +93,8 @@ _SIGS = {
                                    ctypes.POINTER(CgInfo), _vp]),
     "bs_cg_solve_refined_f32": (ctypes.c_int, [_vp, _vp, _vp, _d, _i32, _d, _i32, _i32,
                                                ctypes.POINTER(CgInfo), _vp]),
+    "bs_cg_solve_batched": (ctypes.c_int, [_i32, _vp, _vp, _vp, _d, _i32, _i32,
+                                           ctypes.POINTER(CgInfo), _vp]),
 }
 
 
@@ -325,7 +328,7 @@ class Problem:
         d["rc"] = rc
         return x, d
 
-    def cg_refined_f32(self, b, x=None, tol=1e-10, maxit=100000, inner_tol=1e-4,
+    def cg_refined_f32(self, b, x=None, tol=1e-10, maxit=1000000, inner_tol=1e-4,
                        outer_maxit=50, flags=0, check=True):
         """FP32 CG inside FP64 iterative refinement.  Returns (x, info dict);
         info['rel_residual'] is the FP64 true relative residual."""
@@ -339,3 +342,22 @@ class Problem:
         d = info.as_dict()
         d["rc"] = rc
         return x, d
+
+
+def solve_batched(problems, bs_, xs, tol=1e-8, maxit=1000000, flags=0, check=True):
+    """bs_cg_solve_batched: Algorithm 1 on every (problem, b, x) together.
+    Returns (rc, list of per-solve info dicts)."""
+    n = len(problems)
+    if not (n == len(bs_) == len(xs)) or n == 0:
+        raise ValueError("problems, b and x must be non-empty lists of one length")
+    P = (ctypes.c_void_p * n)(*[p.handle.value for p in problems])
+    B = (ctypes.c_void_p * n)(*[_ptr(b, name="b").value for b in bs_])
+    X = (ctypes.c_void_p * n)(*[_ptr(x, name="x").value for x in xs])
+    infos = (CgInfo * n)()
+    rc = lib().bs_cg_solve_batched(n, ctypes.cast(P, ctypes.c_void_p),
+                                   ctypes.cast(B, ctypes.c_void_p),
+                                   ctypes.cast(X, ctypes.c_void_p), tol, maxit, flags, infos,
+                                   _stream())
+    if check and rc != BS_OK:
+        _check(rc, "bs_cg_solve_batched")
+    return rc, [infos[i].as_dict() for i in range(n)]

@@ -50,20 +50,18 @@ struct EpNone {
   __device__ __forceinline__ void operator()(double) const {}
 };
 
-// qG[g] = sum over k in [rowStarts[g], rowStarts[g+1]) of qL[colIds[k]],
-// serially from +0 in ascending k.  DOT: also reduce sum_g w[g] * qG[g].
-template <typename T, bool DOT, class Ep>
-__global__ void __launch_bounds__(kGatherBlock)
-    k_gather(int64_t ntiles, const int2 *__restrict__ tiles,
-             const int32_t *__restrict__ row_starts, const int32_t *__restrict__ col_ids,
-             const T *__restrict__ qL, T *__restrict__ qG, const T *__restrict__ w,
-             double *partials, unsigned int *counter, Ep ep, const CgState *st) {
+// One tile [lo, hi) of rows: qG[g] = sum over k in [rowStarts[g],
+// rowStarts[g+1]) of qL[colIds[k]], serially from +0 in ascending k; DOT
+// adds w[g] * qG[g] into acc.  A block of kGatherBlock threads calls it
+// together (block barriers inside); s_v holds kTileNnz values.
+template <typename T, bool DOT>
+__device__ __forceinline__ void gather_tile(int2 lo, int2 hi,
+                                            const int32_t *__restrict__ row_starts,
+                                            const int32_t *__restrict__ col_ids,
+                                            const T *__restrict__ qL, T *__restrict__ qG,
+                                            const T *__restrict__ w, T *s_v, Acc<T> &acc) {
   constexpr int U = kTileNnz / kGatherBlock;  // values per thread per tile
-  __shared__ T s_v[kTileNnz];
-  if (cg_halted(st)) return;
-  Acc<T> acc;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int2 lo = tiles[t], hi = tiles[t + 1];
+  {
     const int32_t r0 = lo.x, r1 = hi.x, k0 = lo.y, nk = hi.y - lo.y;
     if (nk <= kTileNnz) {
       int32_t c[U];
@@ -98,6 +96,21 @@ __global__ void __launch_bounds__(kGatherBlock)
       }
     }
   }
+}
+
+// The whole gather, tiles in grid-stride order.  DOT: also reduce
+// sum_g w[g] * qG[g] into ep().
+template <typename T, bool DOT, class Ep>
+__global__ void __launch_bounds__(kGatherBlock)
+    k_gather(int64_t ntiles, const int2 *__restrict__ tiles,
+             const int32_t *__restrict__ row_starts, const int32_t *__restrict__ col_ids,
+             const T *__restrict__ qL, T *__restrict__ qG, const T *__restrict__ w,
+             double *partials, unsigned int *counter, Ep ep, const CgState *st) {
+  __shared__ T s_v[kTileNnz];
+  if (cg_halted(st)) return;
+  Acc<T> acc;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+    gather_tile<T, DOT>(tiles[t], tiles[t + 1], row_starts, col_ids, qL, qG, w, s_v, acc);
   if (DOT) {
     const double part = block_sum<kGatherBlock>(acc.value());
     double total;

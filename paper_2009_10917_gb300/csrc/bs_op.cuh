@@ -36,43 +36,47 @@ struct OpShape {
   static constexpr int THREADS = ((EPB * NQ2 + 31) / 32) * 32;
 };
 
-// out = A_L in  on E elements.  GATHER_IN: in is a global vector read
-// through ids (masked nodes read as 0); else in is element-local.
-// g = c-independent stiffness factor h/2, mlam = lambda (h/2)^3.  Elements
-// are visited in `order` (elements sorted by smallest global index, so the
-// indexed reads of neighbouring elements meet in L2) when it is given.
+// out = A_L in  on elements slot0 .. slot0 + EPB - 1 (slots index `order`
+// when given, else elements directly), by a block of at least
+// OpShape<NQ>::THREADS threads; every thread of the block must call it (it
+// holds block barriers).  GATHER_IN: in is a global vector read through ids
+// (masked nodes read as 0); else in is element-local.  g = h/2 (the
+// c-independent stiffness factor), mlam = lambda (h/2)^3.  Elements visited
+// in `order` (sorted by smallest global index) meet their neighbours' reads
+// in L2.  s_u holds EPB * NQ^3 values, s_K NQ^2, s_w NQ.
 template <typename T, int NQ, bool GATHER_IN>
-__global__ void __launch_bounds__(OpShape<NQ>::THREADS)
-    k_ax_local(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
-               const T *__restrict__ in, T *__restrict__ out, const OpTab<T> *__restrict__ tab,
-               const double *__restrict__ coef, T g, T mlam, const CgState *st) {
+__device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
+                                            const int32_t *__restrict__ order,
+                                            const int32_t *__restrict__ ids,
+                                            const T *__restrict__ in, T *__restrict__ out,
+                                            const OpTab<T> *__restrict__ tab,
+                                            const double *__restrict__ coef, T g, T mlam,
+                                            T *s_u_all, T *s_K, T *s_w) {
   using S = OpShape<NQ>;
-  __shared__ T s_u[S::EPB][S::NP];
-  __shared__ T s_K[NQ * NQ];
-  __shared__ T s_w[NQ];
-  if (cg_halted(st)) return;
+  __syncthreads();  // the shared buffers may still be in use by a previous call
   for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) s_K[t] = tab->K[(t / NQ) * NQ + t % NQ];
   for (int t = threadIdx.x; t < NQ; t += blockDim.x) s_w[t] = tab->w[t];
   const int le = threadIdx.x / S::NQ2;
   const int ij = threadIdx.x - le * S::NQ2;
   const int i = ij % NQ, j = ij / NQ;
-  const int64_t slot = (int64_t)blockIdx.x * S::EPB + le;
+  const int64_t slot = slot0 + le;
   const bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  T *u = s_u_all + (le < S::EPB ? le : 0) * S::NP;
   T ureg[NQ];
   if (active) {
     const int64_t base = e * S::NP + ij;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
-      T u;
+      T v;
       if (GATHER_IN) {
         const int32_t id = __ldcs(ids + base + k * S::NQ2);
-        u = id >= 0 ? in[id] : T(0);
+        v = id >= 0 ? in[id] : T(0);
       } else {
-        u = __ldcs(in + base + k * S::NQ2);
+        v = __ldcs(in + base + k * S::NQ2);
       }
-      ureg[k] = u;
-      s_u[le][ij + k * S::NQ2] = u;
+      ureg[k] = v;
+      u[ij + k * S::NQ2] = v;
     }
   }
   __syncthreads();
@@ -81,7 +85,6 @@ __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
   const T cg = c * g;
   const T wi = s_w[i], wj = s_w[j];
   const T wij = wi * wj;
-  const T *u = s_u[le];
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
     T ar = T(0), as = T(0), at = T(0);
@@ -98,6 +101,20 @@ __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
     const T mass = mlam * (wij * wk) * ureg[k];
     __stcs(out + e * S::NP + ij + k * S::NQ2, fmaT(cg, stiff, mass));
   }
+}
+
+template <typename T, int NQ, bool GATHER_IN>
+__global__ void __launch_bounds__(OpShape<NQ>::THREADS)
+    k_ax_local(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
+               const T *__restrict__ in, T *__restrict__ out, const OpTab<T> *__restrict__ tab,
+               const double *__restrict__ coef, T g, T mlam, const CgState *st) {
+  using S = OpShape<NQ>;
+  __shared__ T s_u[S::EPB * S::NP];
+  __shared__ T s_K[NQ * NQ];
+  __shared__ T s_w[NQ];
+  if (cg_halted(st)) return;
+  ax_elements<T, NQ, GATHER_IN>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out, tab, coef,
+                                g, mlam, s_u, s_K, s_w);
 }
 
 template <typename T, bool GATHER_IN>

@@ -1,0 +1,109 @@
+"""GPU parity of the batched solver: many CG solves of uneven degree and
+size advanced by one cooperative launch per iteration.
+
+Each solve is checked against the FP64 oracle as if it had been run alone:
+relative residual at the tolerance, x against the oracle's CG solution
+(tol 1e-12) within cond(A) * tol (cond < 1e3 on these meshes), and the
+iteration count against the oracle's within 2% (the batched reductions sum
+per-item partials, a different but fixed order).  Repeated runs and the
+CUDA-graph replay give bitwise identical solutions.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_10917_gb300 import bs, synth
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(2, 4), (3, 3), (1, 6), (5, 2), (8, 2), (4, 5), (2, 9), (6, 3), (7, 2), (3, 7), (2, 2)]
+
+
+def make(specs, seed, lam=1.0):
+    out = []
+    for i, (N, K) in enumerate(specs):
+        m = synth.Mesh(K, N, seed=seed + i)
+        Z = bs.Map(m.E, N, m.NG, m.ids)
+        P = bs.Problem(Z, m.h, lam)
+        b = synth.uniform(m.NG, seed + i, stream=3)
+        out.append((m, Z, P, b))
+    return out
+
+
+def run(cases, tol, flags=0, maxit=1000000, check=True):
+    bs_ = [torch.from_numpy(c[3]).cuda() for c in cases]
+    xs = [torch.full_like(b, 7.0) for b in bs_]  # x0 = 0 regardless of contents
+    rc, infos = bs.solve_batched([c[2] for c in cases], bs_, xs, tol=tol, maxit=maxit,
+                                 flags=flags, check=check)
+    return rc, infos, [x.cpu().numpy() for x in xs]
+
+
+def test_batched_fp64_matches_oracle():
+    cases = make(SPECS, 100)
+    rc, infos, xs = run(cases, 1e-10)
+    assert rc == 0
+    for (m, Z, P, b), info, x in zip(cases, infos, xs):
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+        xo, it, *_ = oracle.cg(m.E, m.N, m.h, 1.0, m.ids, m.NG, b, tol=1e-10, maxit=50000)
+        assert abs(info["iterations"] - it) <= max(2, 0.02 * it)
+        xt, *_ = oracle.cg(m.E, m.N, m.h, 1.0, m.ids, m.NG, b, tol=1e-12, maxit=50000)
+        assert np.linalg.norm(x - xt) <= 1e3 * 1e-10 * np.linalg.norm(xt)
+        r = b - oracle.apply_A(m.E, m.N, m.h, 1.0, m.ids, m.NG, x)
+        assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(b)
+
+
+def test_batched_deterministic_and_graph():
+    cases = make(SPECS[:6], 300)
+    _, i1, x1 = run(cases, 1e-9)
+    _, i2, x2 = run(cases, 1e-9)
+    _, i3, x3 = run(cases, 1e-9, flags=bs.BS_CG_GRAPH)
+    for a, b_, c in zip(x1, x2, x3):
+        assert np.array_equal(a, b_) and np.array_equal(a, c)
+    assert [i["iterations"] for i in i1] == [i["iterations"] for i in i3]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batched_refined_f32(graph):
+    cases = make(SPECS, 500)
+    flags = bs.BS_CG_REFINED_F32 | (bs.BS_CG_GRAPH if graph else 0)
+    rc, infos, xs = run(cases, 1e-8, flags=flags)
+    assert rc == 0
+    for (m, Z, P, b), info, x in zip(cases, infos, xs):
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+        r = b - oracle.apply_A(m.E, m.N, m.h, 1.0, m.ids, m.NG, x)
+        assert np.linalg.norm(r) <= 1.5e-8 * np.linalg.norm(b)
+        assert info["outer"] >= 1
+
+
+def test_batched_isolates_a_failing_solve():
+    cases = make(SPECS[:5], 700)
+    cases[2][3][4] = np.nan
+    rc, infos, xs = run(cases, 1e-10, check=False)
+    assert rc == bs.BS_ERR_BREAKDOWN
+    for i, info in enumerate(infos):
+        if i == 2:
+            assert info["status"] == bs.BS_ERR_BREAKDOWN
+        else:
+            assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+
+
+def test_batched_iteration_limit():
+    cases = make(SPECS[:4], 800)
+    rc, infos, _ = run(cases, 1e-14, maxit=5, check=False)
+    assert rc == bs.BS_ERR_NOT_CONVERGED
+    assert all(i["iterations"] == 5 for i in infos)
+
+
+def test_batched_rejects_bad_batches():
+    cases = make([(2, 2), (3, 2)], 900)
+    b = [torch.from_numpy(c[3]).cuda() for c in cases]
+    x = [torch.zeros_like(t) for t in b]
+    with pytest.raises(bs.BSError):
+        bs.solve_batched([cases[0][2], cases[0][2]], [b[0], b[0]], [x[0], x[0]])
+    m = synth.Mesh(1, 9, seed=1)
+    Z = bs.Map(m.E, 9, m.NG, m.ids)
+    P9 = bs.Problem(Z, m.h, 1.0)
+    t = torch.zeros(m.NG, dtype=torch.float64, device="cuda")
+    with pytest.raises(bs.BSError):
+        bs.solve_batched([P9], [t], [t.clone()])
