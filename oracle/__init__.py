@@ -313,3 +313,80 @@ def cg_ir_f32(E, N, h, lam, ids, NG, b, outer_tol=1e-10, outer_maxit=50, inner_t
     if it < 0:
         raise RuntimeError(f"bso_cg_ir_f32 failed ({it})")
     return x, it, outer.value, rel.value
+
+
+# ---------------------------------------------------------------- learned preconditioner
+
+_SIGS.update({
+    "bso_bf16_round": (None, [_i64, _F, _F]),
+    "bso_mlp_forward": (None, [_i64, _int, _int, _F, _F, _F, _D, _D, _int]),
+    "bso_mlp_loss_grad": (_dbl, [_i64, _int, _int, _F, _F, _F, _F, _D, _D, _int]),
+    "bso_adam": (None, [_i64, _F, _F, _F, _F, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                        ctypes.c_float, _int]),
+    "bso_fpcg": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _F, _F, _int, _int, _D, _D, _dbl,
+                        _int, _D, ctypes.POINTER(_int)]),
+})
+
+
+def _lib_mlp():
+    L = lib()
+    for name in ("bso_bf16_round", "bso_mlp_forward", "bso_mlp_loss_grad", "bso_adam", "bso_fpcg"):
+        res, args = _SIGS[name]
+        fn = getattr(L, name)
+        fn.restype, fn.argtypes = res, args
+    return L
+
+
+def bf16_round(a):
+    """Round float values to bfloat16 (nearest even), returned as float32."""
+    a = _f32(a)
+    out = np.empty_like(a)
+    _lib_mlp().bso_bf16_round(a.size, _fp(a), _fp(out))
+    return out
+
+
+def mlp_forward(W1, W2, X, bf16=False):
+    """y = W2 relu(W1 x) per row of X (W1: H x D, W2: D x H).  Returns (Y, hidden)."""
+    W1, W2, X = _f32(W1), _f32(W2), _f32(X)
+    H, D = W1.shape
+    B = X.shape[0]
+    Y, hid = np.empty((B, D)), np.empty((B, H))
+    _lib_mlp().bso_mlp_forward(B, D, H, _fp(W1), _fp(W2), _fp(X), _d(Y), _d(hid), int(bf16))
+    return Y, hid
+
+
+def mlp_loss_grad(W1, W2, X, T, bf16=False):
+    """MSE loss and (dL/dW1, dL/dW2) in FP64."""
+    W1, W2, X, T = _f32(W1), _f32(W2), _f32(X), _f32(T)
+    H, D = W1.shape
+    g1, g2 = np.empty((H, D)), np.empty((D, H))
+    loss = _lib_mlp().bso_mlp_loss_grad(X.shape[0], D, H, _fp(W1), _fp(W2), _fp(X), _fp(T),
+                                        _d(g1), _d(g2), int(bf16))
+    return float(loss), g1, g2
+
+
+def adam(w, g, m, v, lr, t, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in float, in place on copies; returns (w, m, v)."""
+    w, g, m, v = _f32(w).copy(), _f32(g), _f32(m).copy(), _f32(v).copy()
+    _lib_mlp().bso_adam(w.size, _fp(w), _fp(g), _fp(m), _fp(v), lr, b1, b2, eps, int(t))
+    return w, m, v
+
+
+def fpcg(E, N, h, lam, ids, NG, b, W1=None, W2=None, bf16=True, tol=1e-8, maxit=10000,
+         coef=None):
+    """Flexible PCG with the learned correction (W2 None: Jacobi only).
+    Returns (x, iters, rr[], fallbacks)."""
+    ids, b, coef = _ids(ids), _f64(b), _coef(coef)
+    x = np.zeros(int(NG))
+    hr = np.zeros(maxit + 2)
+    fb = ctypes.c_int(0)
+    H = 0 if W1 is None else int(np.asarray(W1).shape[0])
+    W1p = None if W1 is None else _f32(W1)
+    W2p = None if W2 is None else _f32(W2)
+    it = _lib_mlp().bso_fpcg(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG),
+                             None if W1p is None else _fp(W1p),
+                             None if W2p is None else _fp(W2p), H, int(bool(bf16)), _d(b),
+                             _d(x), float(tol), int(maxit), _d(hr), ctypes.byref(fb))
+    if it < 0:
+        raise RuntimeError(f"bso_fpcg failed ({it})")
+    return x, it, hr[:it + 1], fb.value

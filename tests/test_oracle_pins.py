@@ -366,3 +366,101 @@ def test_model_fit_recovers_table2():
             T = perfmodel.time_model(B, T0_us * 1e-6, W * 1e9)
             t0, w = perfmodel.fit(B, T)
             assert abs(t0 - T0_us * 1e-6) < 1e-12 and abs(w / (W * 1e9) - 1) < 1e-9
+
+
+# ------------------------------------------------------------------ learned preconditioner
+
+def _mlp(D=6, H=9, seed=3):
+    W1 = synth.uniform(H * D, seed, 0).reshape(H, D).astype(np.float32)
+    W2 = synth.uniform(D * H, seed, 1).reshape(D, H).astype(np.float32)
+    return W1, W2
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, -2.5, 3.0e38,
+                     1.0 + 2 ** -8 + 2 ** -9], dtype=np.float32)
+    got = oracle.bf16_round(vals)
+    # bfloat16 keeps 8 significant bits: 1 + 2^-8 is a tie -> even (1.0);
+    # 1 + 3*2^-9 rounds up to 1 + 2^-7; 1 + 2^-8 + 2^-9 rounds up too
+    want = np.array([1.0, 1.0, 1.0, 1.0 + 2 ** -7, -2.5, 2.9999748e38, 1.0 + 2 ** -7],
+                    dtype=np.float32)
+    assert np.array_equal(got[:5], want[:5]) and got[6] == want[6]
+    assert abs(got[5] / 3.0e38 - 1) < 2 ** -8
+
+
+def test_mlp_gradients_match_central_differences():
+    W1, W2 = _mlp()
+    X = synth.uniform(5 * 6, 4).reshape(5, 6).astype(np.float32)
+    T = synth.uniform(5 * 6, 5).reshape(5, 6).astype(np.float32)
+    loss, g1, g2 = oracle.mlp_loss_grad(W1, W2, X, T)
+    for W, g, which in ((W1, g1, 0), (W2, g2, 1)):
+        for idx in [(0, 0), (2, 3), (W.shape[0] - 1, W.shape[1] - 1), (1, 4)]:
+            # the oracle takes float weights; difference on a float-exact grid
+            hstep = 2.0 ** -12
+            Wp, Wm = W.copy(), W.copy()
+            Wp[idx] += hstep
+            Wm[idx] -= hstep
+            args_p = (Wp, W2) if which == 0 else (W1, Wp)
+            args_m = (Wm, W2) if which == 0 else (W1, Wm)
+            lp = oracle.mlp_loss_grad(*args_p, X, T)[0]
+            lm = oracle.mlp_loss_grad(*args_m, X, T)[0]
+            fd = (lp - lm) / (2 * hstep)
+            if abs(g[idx]) > 1e-6:
+                assert abs(fd - g[idx]) <= 1e-6 * abs(g[idx]) + 1e-9
+
+
+def test_mlp_positive_homogeneity_and_zero():
+    W1, W2 = _mlp(8, 11, 6)
+    X = synth.uniform(4 * 8, 7).reshape(4, 8).astype(np.float32)
+    y1, _ = oracle.mlp_forward(W1, W2, X)
+    y2, _ = oracle.mlp_forward(W1, W2, 2.0 * X)
+    assert np.array_equal(2.0 * y1, y2)
+    y0, _ = oracle.mlp_forward(W1, np.zeros_like(W2), X)
+    assert np.all(y0 == 0.0)
+    # the hidden layer is relu(W1 x), checked by a plain numpy product
+    _, hid = oracle.mlp_forward(W1, W2, X)
+    np.testing.assert_allclose(hid, np.maximum(X.astype(np.float64) @ W1.T.astype(np.float64),
+                                               0.0), rtol=1e-12, atol=1e-14)
+
+
+def test_adam_first_step_moves_by_lr():
+    w = np.zeros(5, np.float32)
+    g = np.array([1.0, -2.0, 0.5, 1e-3, -1e-4], np.float32)
+    w1, m, v = oracle.adam(w, g, np.zeros(5, np.float32), np.zeros(5, np.float32), 1e-3, 1)
+    # bias-corrected first step is -lr * sign(g) (up to eps)
+    np.testing.assert_allclose(w1, -1e-3 * np.sign(g), rtol=1e-3)
+
+
+def test_fpcg_with_zero_correction_is_jacobi_pcg():
+    m = synth.Mesh(3, 3, seed=2)
+    coef = synth.lognormal(m.E, 4)
+    b = synth.uniform(m.NG, 8)
+    Np = m.Np
+    W1 = synth.uniform(16 * Np, 9).reshape(16, Np).astype(np.float32)
+    W2 = np.zeros((Np, 16), np.float32)
+    x, it, rr, fb = oracle.fpcg(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, W1, W2, tol=1e-10,
+                                maxit=5000, coef=coef)
+    xj, itj, rrj = oracle.pcg_jacobi(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, tol=1e-10, maxit=5000,
+                                     coef=coef)
+    assert abs(it - itj) <= 1
+    assert np.linalg.norm(x - xj) <= 1e-8 * np.linalg.norm(xj)
+    k = min(it, itj, 20)
+    np.testing.assert_allclose(rr[:k], rrj[:k], rtol=1e-8)
+
+
+def test_fpcg_with_exact_local_inverse_beats_jacobi():
+    """A correction that reproduces an element-block solve is a stronger
+    preconditioner than Jacobi: FPCG must then need fewer iterations."""
+    m = synth.Mesh(2, 2, seed=1)
+    A_e = fem_ref.element_matrices(2, m.h)
+    Ae = A_e[0] + 1e-2 * A_e[1]
+    # linear map u -> Ae^-1 (diag(Ae) u) - u, realised exactly with ReLU pairs
+    Np = m.Np
+    Mlin = np.linalg.solve(Ae, np.diag(np.diag(Ae))) - np.eye(Np)
+    W1 = np.concatenate([np.eye(Np), -np.eye(Np)]).astype(np.float32)
+    W2 = np.concatenate([Mlin, -Mlin], axis=1).astype(np.float32)
+    b = synth.uniform(m.NG, 3)
+    _, it, _, fb = oracle.fpcg(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, W1, W2, bf16=False,
+                               tol=1e-10, maxit=2000)
+    _, itj, _ = oracle.pcg_jacobi(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, tol=1e-10, maxit=2000)
+    assert it < itj and fb == 0
