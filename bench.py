@@ -49,9 +49,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-tolerance runs")
-    ap.add_argument("--workload", default="stream", choices=["stream", "cg", "batched"],
+    ap.add_argument("--workload", default="stream",
+                    choices=["stream", "cg", "batched", "learned"],
                     help="stream: the BS step (default); cg: only the CG solves on --cg-mesh; "
-                         "batched: 256 uneven solves, batched vs one at a time")
+                         "batched: 256 uneven solves, batched vs one at a time; "
+                         "learned: learned-preconditioner FPCG vs Jacobi-PCG and plain CG")
+    ap.add_argument("--learned-mesh", default="5,64", help="N,K of the learned workload")
     ap.add_argument("--nsolves", type=int, default=256, help="solves in the batched workload")
     ap.add_argument("--cg-mesh", default="7,48", help="N,K of the CG time-to-tolerance mesh")
     ap.add_argument("--no-cg-small", action="store_true", help="skip the N=3, 8^3 CG runs")
@@ -393,6 +396,63 @@ def batched_section(args):
     return out
 
 
+def learned_section(args):
+    """The learned-preconditioner configuration: degree N=5 on a 64^3 mesh
+    (E = 262144, N_G = 321^3), lambda = 1e-2, per-element coefficient
+    lognormal(sigma = 1), b uniform[-1, 1), tol 1e-8.  Times plain FP64 CG,
+    Jacobi-PCG and flexible PCG with the network trained on the GPU (20000
+    pairs from Jacobi-PCG residuals, 40000 Adam steps), each solve after one
+    untimed warm-up solve; the one-off pair and training times are reported
+    beside them.  Residuals are the FP64 true residuals ||b - A x|| / ||b||."""
+    import torch
+
+    from paper_2009_10917_gb300 import bs, learned, synth
+    N, K = (int(v) for v in args.learned_mesh.split(","))
+    lam = 1e-2
+    m = synth.Mesh(K, N, seed=1)
+    coef = synth.lognormal(m.E, 2)
+    Z = bs.Map(m.E, N, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, lam, coef)
+    b = torch.from_numpy(synth.uniform(m.NG, 4242)).cuda()
+    bn = torch.linalg.norm(b).item()
+
+    def true_rel(x):
+        r = P.apply_A(x)
+        bs.axpy(1.0, b, -1.0, r)
+        return torch.linalg.norm(r).item() / bn
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        x, info = fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        return {"seconds": round(dt, 3), "iterations": info["iterations"],
+                "ms_per_iteration": round(1000 * dt / max(1, info["iterations"]), 4),
+                "rel_residual_true": true_rel(x), "rc": info["rc"]}
+
+    out = {"mesh": f"N={N} {K}^3", "E": m.E, "N_G": m.NG, "lambda": lam,
+           "coef": "lognormal(sigma=1) per element", "tol": 1e-8}
+    out["plain_fp64_cg"] = timed(lambda: P.cg(b, tol=1e-8, maxit=200000, flags=bs.BS_CG_GRAPH,
+                                              check=False))
+    out["jacobi_pcg"] = timed(lambda: P.cg(b, tol=1e-8, maxit=200000,
+                                           flags=bs.BS_CG_GRAPH | bs.BS_CG_JACOBI, check=False))
+    net, meta = learned.build_preconditioner(P, m.E, m.NG, npairs=20000, steps=40000)
+    out["training"] = meta
+    res = timed(lambda: bs.fpcg_learned(P, net, b, tol=1e-8, maxit=200000,
+                                        flags=bs.BS_CG_GRAPH | bs.BS_FPCG_ODD, check=False))
+    out["learned_fpcg_odd"] = res
+    full = timed(lambda: bs.fpcg_learned(P, net, b, tol=1e-8, maxit=200000,
+                                         flags=bs.BS_CG_GRAPH, check=False))
+    out["learned_fpcg_full_network"] = full
+    for k in ("plain_fp64_cg", "jacobi_pcg"):
+        out[f"speedup_learned_vs_{k}"] = round(out[k]["seconds"] / res["seconds"], 3)
+        out[f"iteration_ratio_{k}_over_learned"] = round(
+            out[k]["iterations"] / max(1, res["iterations"]), 3)
+    return out
+
+
 def run_cg_only(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -493,5 +553,11 @@ if __name__ == "__main__":
         print(json.dumps({"metric": "time-to-1e-8 CG solve, batched vs one at a time",
                           "unit": "s", "higher_is_better": False,
                           "batched": batched_section(a)}), flush=True)
+    elif a.workload == "learned":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"metric": "time-to-1e-8 CG solve, learned FPCG vs Jacobi-PCG",
+                          "unit": "s", "higher_is_better": False,
+                          "learned": learned_section(a)}), flush=True)
     else:
         run_ours(a)

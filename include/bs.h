@@ -181,7 +181,7 @@ typedef struct {
   int32_t iterations;   /* CG iterations performed                        */
   int32_t status;       /* bs_status of the solve                         */
   int32_t outer;        /* refinement steps (bs_cg_solve_refined_f32)     */
-  int32_t reserved;
+  int32_t fallbacks;    /* learned FPCG: corrections replaced by Jacobi   */
   double rr;            /* final r.r (recursive residual)                 */
   double bb;            /* b.b                                            */
   double rel_residual;  /* sqrt(rr / bb); FP64 true residual when refined */
@@ -242,6 +242,90 @@ int bs_cg_solve_batched(int32_t nsolves, const bs_problem *const *probs,
                         const double *const *b, double *const *x, double tol,
                         int32_t maxit, int32_t flags, bs_cg_info *infos,
                         void *stream);
+
+/* ------------------------------------------------------------ learned preconditioner */
+
+/* A per-element network for a flexible PCG preconditioner.  The paper has no
+ * learned part; everything in this section is this library's own definition.
+ *
+ * Network: y = W2 relu(W1 x), W1 [H x D], W2 [D x H] row-major FP32 masters,
+ * no biases, D = (N+1)^3 values of one element.  Products run on the BF16
+ * tensor cores with FP32 accumulation: in BF16 mode weights and activations
+ * are single bf16 values; with BS_MLP_BF16X3 each is carried as hi + lo
+ * (hi = bf16(v), lo = bf16(v - hi)) and a product is ahi bhi + ahi blo +
+ * alo bhi, about 2^-16 relative instead of 2^-8.  Training is Adam on the
+ * mean squared error, all in the library's kernels.
+ *
+ * Odd part: for a bias-free ReLU network, (f(x) - f(-x)) / 2 = W2 W1 x / 2
+ * (relu(a) - relu(-a) = a) -- a LINEAR map.  BS_MLP_ODD / BS_FPCG_ODD
+ * evaluate that instead of f; a Krylov method needs its preconditioner to be
+ * (near) linear, and training on sign-symmetric pairs drives f's even part
+ * W2 |W1 x| / 2 towards zero anyway. */
+typedef struct bs_mlp bs_mlp;
+
+enum {
+  BS_MLP_BF16X3 = 1, /* bs_mlp_create: hi + lo bf16 operands (three products) */
+  BS_MLP_ODD = 2,    /* bs_mlp_forward: the odd part W2 W1 x / 2              */
+  BS_FPCG_ODD = 64   /* bs_fpcg_learned: precondition with the odd part       */
+};
+
+/* Create a network from HOST weights h_W1 [H x D], h_W2 [D x H] (copied).
+ * 1 <= D <= 4096; H a multiple of 32 in [32, 4096].  flags: 0 or
+ * BS_MLP_BF16X3.  Synchronous.  Adam state starts at zero. */
+int bs_mlp_create(int32_t D, int32_t H, const float *h_W1, const float *h_W2,
+                  int32_t flags, bs_mlp **out);
+int bs_mlp_destroy(bs_mlp *mlp);
+/* Copy the FP32 master weights to HOST h_W1 [H x D], h_W2 [D x H] (either
+ * may be NULL).  Synchronous. */
+int bs_mlp_get_weights(const bs_mlp *mlp, float *h_W1, float *h_W2);
+/* d_Y [B x D] = f(d_X [B x D]) (DEVICE float), or the odd part with
+ * BS_MLP_ODD.  Scratch for B rows is allocated on first use and kept. */
+int bs_mlp_forward(bs_mlp *mlp, int64_t B, const float *d_X, float *d_Y,
+                   int32_t flags, void *stream);
+/* Mean squared error L = sum (f(x) - t)^2 / (B D) over a batch d_X, d_T
+ * [B x D] into d_loss[0] (DEVICE double), and dL/dW1 [H x D], dL/dW2
+ * [D x H] into d_gW1, d_gW2 (DEVICE float, may be NULL).  B a positive
+ * multiple of 32.  The backward products use bf16 (hi) operands. */
+int bs_mlp_loss_grad(bs_mlp *mlp, int64_t B, const float *d_X, const float *d_T,
+                     double *d_loss, float *d_gW1, float *d_gW2, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr > 0)
+ * on the batch; d_loss[0] receives the batch loss before the step. */
+int bs_mlp_train_step(bs_mlp *mlp, int64_t B, const float *d_X, const float *d_T,
+                      float lr, double *d_loss, void *stream);
+
+/* Training pairs from a global residual d_r [N_G] (DEVICE): for pair q and
+ * element e = d_elems[q] (DEVICE int32), with u = diag(A)^-1 r on the
+ * element's (N+1)^3 nodes and rms = sqrt(mean u^2):
+ *   d_X[q] = s u / rms,   d_T[q] = s (e_I - u_I) / rms on interior nodes
+ *   (1 <= i,j,k <= N-1), 0 on the others,
+ * where e_I solves A_II e_I = r_I, A_II the interior block of
+ * c_e S_e + lambda M_e: the element-interior error, i.e. the correction
+ * that zeroes the residual on the element's interior with its other nodes
+ * held.  e_I comes from Jacobi-preconditioned CG on that element, run by one
+ * thread block to a relative residual of 1e-13 (at most 4 (N-1)^3
+ * iterations).  s = -1 for odd q when negate_odd (the pair (-r, -e) is as
+ * valid as (r, e)), else 1; rms = 0 gives zero rows.  d_X, d_T are DEVICE
+ * float [count x (N+1)^3].  Degrees 2..8. */
+int bs_mlp_pairs(const bs_problem *prob, const double *d_r, int64_t count,
+                 const int32_t *d_elems, int32_t negate_odd, float *d_X, float *d_T,
+                 void *stream);
+
+/* Flexible PCG with the learned correction, x0 = 0:
+ *   z = M(r) = D^-1 r + v^-1 Z^T y,  y_e = rms_e g(Z D^-1 r / rms_e)_e
+ * with g = f, or its odd part with BS_FPCG_ODD, v the node valences;
+ * alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap; beta = r.(z' - z) /
+ * (r.z)_old (Polak-Ribiere); p = z' + beta p.  mlp == NULL gives Jacobi-PCG.
+ * Jacobi is the fallback and the judge: an iteration whose r.z' <= 0 (or not
+ * finite) uses z' = D^-1 r (counted in info->fallbacks), and if r.r has not
+ * fallen by 4 within 256 iterations the solve restarts from the current x
+ * with Jacobi for good (info->outer = the iteration of that switch, 0 if
+ * none).  Stop: r.r <= tol^2 b.b or maxit.  flags: BS_CG_GRAPH,
+ * BS_FPCG_ODD.  The network's input size must be (N+1)^3.  Synchronises
+ * `stream`.  Returns BS_ERR_NOT_CONVERGED or BS_ERR_BREAKDOWN as
+ * bs_cg_solve does. */
+int bs_fpcg_learned(const bs_problem *prob, bs_mlp *mlp, const double *b, double *x,
+                    double tol, int32_t maxit, int32_t flags, bs_cg_info *info,
+                    void *stream);
 
 /* ------------------------------------------------------------ no allocation */
 

@@ -319,18 +319,21 @@ def cg_ir_f32(E, N, h, lam, ids, NG, b, outer_tol=1e-10, outer_maxit=50, inner_t
 
 _SIGS.update({
     "bso_bf16_round": (None, [_i64, _F, _F]),
-    "bso_mlp_forward": (None, [_i64, _int, _int, _F, _F, _F, _D, _D, _int]),
+    "bso_mlp_forward": (None, [_i64, _int, _int, _F, _F, _F, _D, _D, _int, _int]),
     "bso_mlp_loss_grad": (_dbl, [_i64, _int, _int, _F, _F, _F, _F, _D, _D, _int]),
     "bso_adam": (None, [_i64, _F, _F, _F, _F, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                         ctypes.c_float, _int]),
-    "bso_fpcg": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _F, _F, _int, _int, _D, _D, _dbl,
-                        _int, _D, ctypes.POINTER(_int)]),
+    "bso_fpcg": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _F, _F, _int, _int, _int, _D, _D,
+                        _dbl, _int, _D, ctypes.POINTER(_int)]),
+    "bso_interior_pairs": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _i64, _I, _int, _F,
+                                  _F]),
 })
 
 
 def _lib_mlp():
     L = lib()
-    for name in ("bso_bf16_round", "bso_mlp_forward", "bso_mlp_loss_grad", "bso_adam", "bso_fpcg"):
+    for name in ("bso_bf16_round", "bso_mlp_forward", "bso_mlp_loss_grad", "bso_adam", "bso_fpcg",
+                 "bso_interior_pairs"):
         res, args = _SIGS[name]
         fn = getattr(L, name)
         fn.restype, fn.argtypes = res, args
@@ -345,23 +348,29 @@ def bf16_round(a):
     return out
 
 
-def mlp_forward(W1, W2, X, bf16=False):
-    """y = W2 relu(W1 x) per row of X (W1: H x D, W2: D x H).  Returns (Y, hidden)."""
+PREC_FP64, PREC_BF16, PREC_BF16X3 = 0, 1, 2
+
+
+def mlp_forward(W1, W2, X, prec=PREC_FP64, odd=False):
+    """y = W2 relu(W1 x) per row of X (W1: H x D, W2: D x H), or its odd part
+    (f(x) - f(-x)) / 2 when odd.  prec: PREC_FP64, PREC_BF16 or PREC_BF16X3.
+    Returns (Y, hidden of f(x))."""
     W1, W2, X = _f32(W1), _f32(W2), _f32(X)
     H, D = W1.shape
     B = X.shape[0]
     Y, hid = np.empty((B, D)), np.empty((B, H))
-    _lib_mlp().bso_mlp_forward(B, D, H, _fp(W1), _fp(W2), _fp(X), _d(Y), _d(hid), int(bf16))
+    _lib_mlp().bso_mlp_forward(B, D, H, _fp(W1), _fp(W2), _fp(X), _d(Y), _d(hid), int(prec),
+                               int(bool(odd)))
     return Y, hid
 
 
-def mlp_loss_grad(W1, W2, X, T, bf16=False):
-    """MSE loss and (dL/dW1, dL/dW2) in FP64."""
+def mlp_loss_grad(W1, W2, X, T, prec=PREC_FP64):
+    """MSE loss and (dL/dW1, dL/dW2) in FP64 (forward in mode prec)."""
     W1, W2, X, T = _f32(W1), _f32(W2), _f32(X), _f32(T)
     H, D = W1.shape
     g1, g2 = np.empty((H, D)), np.empty((D, H))
     loss = _lib_mlp().bso_mlp_loss_grad(X.shape[0], D, H, _fp(W1), _fp(W2), _fp(X), _fp(T),
-                                        _d(g1), _d(g2), int(bf16))
+                                        _d(g1), _d(g2), int(prec))
     return float(loss), g1, g2
 
 
@@ -372,8 +381,8 @@ def adam(w, g, m, v, lr, t, b1=0.9, b2=0.999, eps=1e-8):
     return w, m, v
 
 
-def fpcg(E, N, h, lam, ids, NG, b, W1=None, W2=None, bf16=True, tol=1e-8, maxit=10000,
-         coef=None):
+def fpcg(E, N, h, lam, ids, NG, b, W1=None, W2=None, prec=PREC_BF16, odd=False, tol=1e-8,
+         maxit=10000, coef=None):
     """Flexible PCG with the learned correction (W2 None: Jacobi only).
     Returns (x, iters, rr[], fallbacks)."""
     ids, b, coef = _ids(ids), _f64(b), _coef(coef)
@@ -385,8 +394,24 @@ def fpcg(E, N, h, lam, ids, NG, b, W1=None, W2=None, bf16=True, tol=1e-8, maxit=
     W2p = None if W2 is None else _f32(W2)
     it = _lib_mlp().bso_fpcg(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG),
                              None if W1p is None else _fp(W1p),
-                             None if W2p is None else _fp(W2p), H, int(bool(bf16)), _d(b),
-                             _d(x), float(tol), int(maxit), _d(hr), ctypes.byref(fb))
+                             None if W2p is None else _fp(W2p), H, int(prec), int(bool(odd)),
+                             _d(b), _d(x), float(tol), int(maxit), _d(hr), ctypes.byref(fb))
     if it < 0:
         raise RuntimeError(f"bso_fpcg failed ({it})")
     return x, it, hr[:it + 1], fb.value
+
+
+def interior_pairs(E, N, h, lam, ids, NG, r, elems, negate_odd=False, coef=None):
+    """Training pairs (X, T), each [len(elems) x (N+1)^3] float32: X = s u / rms,
+    T = s (A_II^-1 r_I - u_I) / rms on interior nodes (0 elsewhere), u = D^-1 r."""
+    ids, r, coef = _ids(ids), _f64(r), _coef(coef)
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    Np = (N + 1) ** 3
+    X = np.zeros((len(elems), Np), np.float32)
+    T = np.zeros((len(elems), Np), np.float32)
+    rc = _lib_mlp().bso_interior_pairs(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG),
+                                       _d(r), len(elems), _i(elems), int(bool(negate_odd)),
+                                       _fp(X), _fp(T))
+    if rc:
+        raise RuntimeError(f"bso_interior_pairs failed ({rc})")
+    return X, T

@@ -330,6 +330,96 @@ int bso_diag_A(int E, int N, double h, double lambda, const double *coef,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Training pairs of the learned element preconditioner (no counterpart in  */
+/* the paper; the definition this project chose).  For a global residual r  */
+/* and element e, with u = D^-1 r (D = diag A) read through the map:        */
+/*   rms   = sqrt(mean over the element's Np nodes of u^2)                  */
+/*   e_I   = A_II^-1 r_I : the element-interior error, i.e. the correction  */
+/*           that zeroes the residual on the element's interior nodes       */
+/*           (1 <= i,j,k <= N-1, not masked) with its other nodes held;     */
+/*           A_II is the interior block of c_e S_e + lambda M_e             */
+/*   X     = s u / rms,  T = s (e_I - u_I) / rms on interior nodes, 0 else  */
+/* with s = -1 for odd pair index when negate_odd (the sign-flipped pair    */
+/* (-r, -e) is as valid as (r, e)), else s = 1; rms = 0 gives zero rows.    */
+/* A_II is formed column by column with element_apply and solved by a       */
+/* dense Cholesky factorisation.  Returns 0, 1 on a bad degree, 2 on an     */
+/* allocation failure, 3 if an A_II is not positive definite.               */
+/* ------------------------------------------------------------------------ */
+int bso_interior_pairs(int E, int N, double h, double lambda, const double *coef,
+                       const int32_t *ids, int64_t NG, const double *rG, int64_t count,
+                       const int32_t *elems, int negate_odd, float *X, float *T) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  double r[33], w[33], D[33 * 33];
+  if (bso_gll(N, r, w, D)) return 1;
+  bso_problem P = {E, N, h, lambda, coef, ids, NG};
+  double *dg = malloc(sizeof(double) * (NG > 0 ? NG : 1));
+  double *buf = malloc(sizeof(double) * ((size_t)Np * Np + 7 * (size_t)Np));
+  int *I = malloc(sizeof(int) * Np);
+  if (!dg || !buf || !I) { free(dg); free(buf); free(I); return 2; }
+  double *Aii = buf, *u = Aii + (size_t)Np * Np, *unit = u + Np, *col = unit + Np,
+         *t1 = col + Np, *t2 = t1 + Np, *t3 = t2 + Np, *y = t3 + Np;
+  bso_diag_A(E, N, h, lambda, coef, ids, NG, dg);
+  int rc = 0;
+  for (int64_t q = 0; q < count && !rc; ++q) {
+    const int e = elems[q];
+    const int32_t *id = ids + (int64_t)e * Np;
+    const double s = (negate_odd && (q & 1)) ? -1.0 : 1.0;
+    double ss = 0.0;
+    for (int l = 0; l < Np; ++l) {
+      u[l] = id[l] >= 0 ? rG[id[l]] / dg[id[l]] : 0.0;
+      ss += u[l] * u[l];
+    }
+    const double rms = sqrt(ss / Np);
+    float *xo = X + q * Np, *to = T + q * Np;
+    for (int l = 0; l < Np; ++l) xo[l] = to[l] = 0.0f;
+    if (!(rms > 0.0)) continue;
+    int nI = 0;
+    for (int k = 1; k < N; ++k)
+      for (int j = 1; j < N; ++j)
+        for (int i = 1; i < N; ++i) {
+          const int l = i + Nq * (j + Nq * k);
+          if (id[l] >= 0) I[nI++] = l;
+        }
+    /* A_II, column c = interior rows of A_e applied to unit vector c */
+    for (int c = 0; c < nI; ++c) {
+      for (int l = 0; l < Np; ++l) unit[l] = 0.0;
+      unit[I[c]] = 1.0;
+      element_apply(&P, r, w, D, e, unit, col, t1, t2, t3);
+      for (int a = 0; a < nI; ++a) Aii[a * nI + c] = col[I[a]];
+    }
+    /* Cholesky A_II = L L^T in place (lower triangle) */
+    for (int c = 0; c < nI && !rc; ++c) {
+      double d = Aii[c * nI + c];
+      for (int k = 0; k < c; ++k) d -= Aii[c * nI + k] * Aii[c * nI + k];
+      if (!(d > 0.0)) { rc = 3; break; }
+      d = sqrt(d);
+      Aii[c * nI + c] = d;
+      for (int a = c + 1; a < nI; ++a) {
+        double v = Aii[a * nI + c];
+        for (int k = 0; k < c; ++k) v -= Aii[a * nI + k] * Aii[c * nI + k];
+        Aii[a * nI + c] = v / d;
+      }
+    }
+    if (rc) break;
+    /* forward then backward substitution on r_I */
+    for (int a = 0; a < nI; ++a) {
+      double v = rG[id[I[a]]];
+      for (int k = 0; k < a; ++k) v -= Aii[a * nI + k] * y[k];
+      y[a] = v / Aii[a * nI + a];
+    }
+    for (int a = nI - 1; a >= 0; --a) {
+      double v = y[a];
+      for (int k = a + 1; k < nI; ++k) v -= Aii[k * nI + a] * y[k];
+      y[a] = v / Aii[a * nI + a];
+    }
+    for (int l = 0; l < Np; ++l) xo[l] = (float)(s * u[l] / rms);
+    for (int a = 0; a < nI; ++a) to[I[a]] = (float)(s * (y[a] - u[I[a]]) / rms);
+  }
+  free(dg); free(buf); free(I);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Conjugate gradients (Algorithm 1) on A u = b.                            */
 /* x holds the initial guess on entry and the solution on exit.             */
 /* Iterates until r.r <= tol^2 (b.b) or maxit; with fixed_iters != 0 runs   */

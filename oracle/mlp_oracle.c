@@ -7,21 +7,34 @@
  * The paper has no learned part; these are the definitions this project
  * chose (listed in the design notes):
  *   MLP:  y = W2 relu(W1 x),  W1: H x D,  W2: D x H (row-major, no biases)
- *   BF16 mode: x, W1, W2 and the hidden activations are rounded to bfloat16
- *         (round to nearest even from the float value) where the GPU rounds
- *         them; everything else is FP64 here.
+ *   Precision modes (prec) of the network's products:
+ *     0  FP64 products of the float values;
+ *     1  BF16: x, W1, W2 and the hidden activations rounded to bfloat16
+ *        (round to nearest even from the float value) where the GPU rounds
+ *        them; sums in FP64 here;
+ *     2  BF16x3: each of those values v carried as hi + lo with
+ *        hi = bf16(v), lo = bf16(v - hi) (the float difference is exact);
+ *        a product a b is ahi bhi + ahi blo + alo bhi (lo lo dropped); the
+ *        hidden sum is rounded to float before its split, as the GPU's FP32
+ *        accumulator is.
+ *   Odd part: f_odd(x) = (f(x) - f(-x)) / 2, evaluated literally; for a
+ *         bias-free ReLU network it equals W2 W1 x / 2 (relu(a) - relu(-a)
+ *         = a), a linear map.
+ *   Backward (loss gradients): in modes 1 and 2 the backward products use
+ *         bf16 copies (hi parts) of x, W2 and the hidden activations.
  *   Loss: L = sum over batch and outputs of (y - t)^2 / (B D).
  *   Adam (Kingma & Ba 2015): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  *         w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), in float.
  *   Preconditioner: u = Z (D^-1 r); per element rms_e = sqrt(mean u_e^2);
- *         y_e = rms_e MLP(u_e / rms_e) (0 where rms_e = 0);
+ *         y_e = rms_e MLP(u_e / rms_e) (0 where rms_e = 0), MLP = f or f_odd;
  *         z = D^-1 r + v^-1 (Z^T y), v the valence of each global node.
  *   FPCG: alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap;
  *         z' = M(r); if r.z' <= 0 or not finite, z' = D^-1 r;
  *         beta = r.(z' - z) / (r_old.z_old); p = z' + beta p.
  *
  * Parity pinned by tests/test_oracle_pins.py (finite differences, positive
- * homogeneity, FPCG with W2 = 0 against Jacobi-PCG).
+ * homogeneity, the odd part against W2 W1 x / 2, the BF16x3 error bound,
+ * FPCG with W2 = 0 against Jacobi-PCG).
  */
 #include <math.h>
 #include <stdint.h>
@@ -49,25 +62,57 @@ void bso_bf16_round(int64_t n, const float *in, float *out) {
 
 static double rnd(double v, int bf16) { return bf16 ? (double)bf16_round((float)v) : v; }
 
-/* y[B x D] = W2 relu(W1 x); hid (optional, B x H) receives relu(W1 x) as used. */
-void bso_mlp_forward(int64_t B, int D, int H, const float *W1, const float *W2,
-                     const float *X, double *Y, double *hid, int bf16) {
-  double *h = malloc(sizeof(double) * H);
-  if (!h) return;
-  for (int64_t b = 0; b < B; ++b) {
-    const float *x = X + b * D;
+/* a b in precision mode prec (a, b already float values in modes 1 and 2) */
+static double prod(double a, double b, int prec) {
+  if (prec == 0) return a * b;
+  if (prec == 1) return rnd(a, 1) * rnd(b, 1);
+  const float af = (float)a, bf = (float)b;
+  const float ah = bf16_round(af), bh = bf16_round(bf);
+  const double al = bf16_round(af - ah), bl = bf16_round(bf - bh);
+  return (double)ah * bh + (double)ah * bl + al * (double)bh;
+}
+
+/* the hidden value as the next layer sees it (before its product rounding) */
+static double hidden_val(double s, int prec) {
+  if (prec == 0) return s;
+  return prec == 1 ? rnd((float)s, 1) : (double)(float)s;
+}
+
+/* one row: y = f(x) (odd = 0) or f_odd(x) = (f(x) - f(-x)) / 2 (odd = 1);
+ * h (H values) receives the hidden activations of f(x). */
+static void forward_row(int D, int H, const float *W1, const float *W2, const float *x,
+                        double *y, double *h, double *h2, int prec, int odd) {
+  for (int pass = 0; pass < 1 + odd; ++pass) {
+    const double sgn = pass ? -1.0 : 1.0;
+    double *hh = pass ? h2 : h;
     for (int j = 0; j < H; ++j) {
       double s = 0.0;
-      for (int i = 0; i < D; ++i) s += rnd(W1[j * D + i], bf16) * rnd(x[i], bf16);
-      s = s > 0.0 ? s : 0.0;
-      h[j] = bf16 ? rnd((float)s, 1) : s;
-      if (hid) hid[b * H + j] = h[j];
+      for (int i = 0; i < D; ++i) s += prod(W1[j * D + i], sgn * x[i], prec);
+      hh[j] = hidden_val(s > 0.0 ? s : 0.0, prec);
     }
-    for (int i = 0; i < D; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < H; ++j) s += rnd(W2[i * H + j], bf16) * h[j];
-      Y[b * D + i] = s;
+  }
+  for (int i = 0; i < D; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < H; ++j) s += prod(W2[i * H + j], h[j], prec);
+    if (odd) {
+      double s2 = 0.0;
+      for (int j = 0; j < H; ++j) s2 += prod(W2[i * H + j], h2[j], prec);
+      s = (s - s2) / 2.0;
     }
+    y[i] = s;
+  }
+}
+
+/* y[B x D] = f(x) or f_odd(x) per row; hid (optional, B x H) receives the
+ * hidden activations of f(x) as used. */
+void bso_mlp_forward(int64_t B, int D, int H, const float *W1, const float *W2,
+                     const float *X, double *Y, double *hid, int prec, int odd) {
+  double *h = malloc(sizeof(double) * 2 * H);
+  if (!h) return;
+  for (int64_t b = 0; b < B; ++b) {
+    forward_row(D, H, W1, W2, X + b * D, Y + b * D, h, h + H, prec, odd);
+    if (hid)
+      for (int j = 0; j < H; ++j) hid[b * H + j] = h[j];
   }
   free(h);
 }
@@ -75,7 +120,8 @@ void bso_mlp_forward(int64_t B, int D, int H, const float *W1, const float *W2,
 /* MSE loss and gradients dL/dW1 (H x D), dL/dW2 (D x H). */
 double bso_mlp_loss_grad(int64_t B, int D, int H, const float *W1, const float *W2,
                          const float *X, const float *T, double *gW1, double *gW2,
-                         int bf16) {
+                         int prec) {
+  const int bf16 = prec != 0;
   double *y = malloc(sizeof(double) * D), *h = malloc(sizeof(double) * H);
   double *dy = malloc(sizeof(double) * D), *dh = malloc(sizeof(double) * H);
   if (!y || !h || !dy || !dh) { free(y); free(h); free(dy); free(dh); return NAN; }
@@ -85,12 +131,13 @@ double bso_mlp_loss_grad(int64_t B, int D, int H, const float *W1, const float *
   const double scale = 2.0 / ((double)B * D);
   for (int64_t b = 0; b < B; ++b) {
     const float *x = X + b * D;
-    bso_mlp_forward(1, D, H, W1, W2, x, y, h, bf16);
+    bso_mlp_forward(1, D, H, W1, W2, x, y, h, prec, 0);
     for (int i = 0; i < D; ++i) {
       const double e = y[i] - T[b * D + i];
       loss += e * e;
       dy[i] = scale * e;
     }
+    for (int j = 0; j < H; ++j) h[j] = rnd(h[j], bf16);
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < H; ++j) gW2[i * H + j] += dy[i] * h[j];
     for (int j = 0; j < H; ++j) {
@@ -127,8 +174,8 @@ int bso_diag_A(int E, int N, double h, double lambda, const double *coef,
 
 /* z = D^-1 r + v^-1 Z^T (rms MLP(Z D^-1 r / rms)); W2 == NULL: z = D^-1 r. */
 static void precond(int E, int Np, const int32_t *ids, int64_t NG, const double *dg,
-                    const double *val, const float *W1, const float *W2, int H, int bf16,
-                    const double *r, double *z) {
+                    const double *val, const float *W1, const float *W2, int H, int prec,
+                    int odd, const double *r, double *z) {
   for (int64_t g = 0; g < NG; ++g) z[g] = r[g] / dg[g];
   if (!W2) return;
   float *x = malloc(sizeof(float) * Np);
@@ -144,7 +191,7 @@ static void precond(int E, int Np, const int32_t *ids, int64_t NG, const double 
     const double rms = sqrt(ss / Np);
     if (!(rms > 0.0)) continue;
     for (int l = 0; l < Np; ++l) x[l] = (float)((id[l] >= 0 ? z[id[l]] : 0.0) / rms);
-    bso_mlp_forward(1, Np, H, W1, W2, x, y, NULL, bf16);
+    bso_mlp_forward(1, Np, H, W1, W2, x, y, NULL, prec, odd);
     for (int l = 0; l < Np; ++l)
       if (id[l] >= 0) corr[id[l]] += rms * y[l];
   }
@@ -161,7 +208,8 @@ static double dot(int64_t n, const double *a, const double *b) {
 /* Flexible PCG; returns iterations (or -1 breakdown, -2 alloc); *fallbacks
  * counts iterations whose correction was rejected. */
 int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const int32_t *ids,
-             int64_t NG, const float *W1, const float *W2, int H, int bf16, const double *b,
+             int64_t NG, const float *W1, const float *W2, int H, int prec, int odd,
+             const double *b,
              double *x, double tol, int maxit, double *hist_rr, int *fallbacks) {
   const int Np = (N + 1) * (N + 1) * (N + 1);
   double *buf = malloc(sizeof(double) * 7 * NG);
@@ -175,7 +223,7 @@ int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const in
   for (int64_t g = 0; g < NG; ++g) x[g] = 0.0;
   for (int64_t g = 0; g < NG; ++g) r[g] = b[g];
   int fb = 0;
-  precond(E, Np, ids, NG, dg, val, W1, W2, H, bf16, r, z);
+  precond(E, Np, ids, NG, dg, val, W1, W2, H, prec, odd, r, z);
   double rz = dot(NG, r, z);
   if (!(rz > 0.0) || !isfinite(rz)) {
     for (int64_t g = 0; g < NG; ++g) z[g] = r[g] / dg[g];
@@ -200,7 +248,7 @@ int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const in
     ++j;
     if (hist_rr) hist_rr[j] = rr;
     if (rr <= eps) break;
-    precond(E, Np, ids, NG, dg, val, W1, W2, H, bf16, r, zn);
+    precond(E, Np, ids, NG, dg, val, W1, W2, H, prec, odd, r, zn);
     double rzn = dot(NG, r, zn);
     if (!(rzn > 0.0) || !isfinite(rzn)) {
       for (int64_t g = 0; g < NG; ++g) zn[g] = r[g] / dg[g];

@@ -33,6 +33,9 @@ BS_CG_JACOBI = 2
 BS_CG_GRAPH = 4
 BS_CG_X0 = 8
 BS_CG_REFINED_F32 = 32
+BS_MLP_BF16X3 = 1
+BS_MLP_ODD = 2
+BS_FPCG_ODD = 64
 
 
 class BSError(RuntimeError):
@@ -43,12 +46,12 @@ class BSError(RuntimeError):
 
 class CgInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("outer", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("outer", ctypes.c_int32), ("fallbacks", ctypes.c_int32),
                 ("rr", ctypes.c_double), ("bb", ctypes.c_double),
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _vp = ctypes.c_void_p
@@ -361,3 +364,118 @@ def solve_batched(problems, bs_, xs, tol=1e-8, maxit=1000000, flags=0, check=Tru
     if check and rc != BS_OK:
         _check(rc, "bs_cg_solve_batched")
     return rc, [infos[i].as_dict() for i in range(n)]
+
+
+# ---------------------------------------------------------------- learned preconditioner
+
+_SIGS.update({
+    "bs_mlp_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _pp]),
+    "bs_mlp_destroy": (ctypes.c_int, [_vp]),
+    "bs_mlp_get_weights": (ctypes.c_int, [_vp, _vp, _vp]),
+    "bs_mlp_forward": (ctypes.c_int, [_vp, _i64, _vp, _vp, _i32, _vp]),
+    "bs_mlp_loss_grad": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bs_mlp_train_step": (ctypes.c_int, [_vp, _i64, _vp, _vp, _f, _vp, _vp]),
+    "bs_mlp_pairs": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp]),
+    "bs_fpcg_learned": (ctypes.c_int, [_vp, _vp, _vp, _vp, _d, _i32, _i32,
+                                       ctypes.POINTER(CgInfo), _vp]),
+})
+
+
+def _bind(names):
+    L = lib()
+    for n in names:
+        res, args = _SIGS[n]
+        f = getattr(L, n)
+        f.restype, f.argtypes = res, args
+    return L
+
+
+def _fptr(t, name="tensor"):
+    return _ptr(t, torch.float32, name)
+
+
+class MLP:
+    """The element network y = W2 relu(W1 x) (bs_mlp): W1 [H x D], W2 [D x H]
+    given as host float32 arrays (the caller draws the initial weights).
+    split: BF16x3 operands (hi + lo bf16, three products) instead of BF16."""
+
+    def __init__(self, W1, W2, split=False):
+        W1 = np.ascontiguousarray(W1, dtype=np.float32)
+        W2 = np.ascontiguousarray(W2, dtype=np.float32)
+        H, D = W1.shape
+        if W2.shape != (D, H):
+            raise ValueError("W2 must be D x H")
+        L = _bind(["bs_mlp_create", "bs_mlp_destroy", "bs_mlp_get_weights", "bs_mlp_forward",
+                   "bs_mlp_loss_grad", "bs_mlp_train_step", "bs_mlp_pairs", "bs_fpcg_learned"])
+        h = ctypes.c_void_p()
+        _check(L.bs_mlp_create(D, H, W1.ctypes.data_as(ctypes.c_void_p),
+                               W2.ctypes.data_as(ctypes.c_void_p),
+                               BS_MLP_BF16X3 if split else 0, ctypes.byref(h)),
+               "bs_mlp_create")
+        self.handle, self.D, self.H, self.split = h, D, H, bool(split)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bs_mlp_destroy(self.handle)
+            self.handle = None
+
+    def weights(self):
+        W1 = np.empty((self.H, self.D), np.float32)
+        W2 = np.empty((self.D, self.H), np.float32)
+        _check(lib().bs_mlp_get_weights(self.handle, W1.ctypes.data_as(ctypes.c_void_p),
+                                        W2.ctypes.data_as(ctypes.c_void_p)), "bs_mlp_get_weights")
+        return W1, W2
+
+    def forward(self, X, odd=False):
+        """f(X) row by row, or its odd part W2 W1 x / 2."""
+        Y = torch.empty_like(X)
+        _check(lib().bs_mlp_forward(self.handle, X.shape[0], _fptr(X, "X"), _fptr(Y, "Y"),
+                                    BS_MLP_ODD if odd else 0, _stream()), "bs_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T):
+        loss = torch.zeros(1, dtype=torch.float64, device=X.device)
+        g1 = torch.empty((self.H, self.D), dtype=torch.float32, device=X.device)
+        g2 = torch.empty((self.D, self.H), dtype=torch.float32, device=X.device)
+        _check(lib().bs_mlp_loss_grad(self.handle, X.shape[0], _fptr(X, "X"), _fptr(T, "T"),
+                                      _ptr(loss), _fptr(g1), _fptr(g2), _stream()),
+               "bs_mlp_loss_grad")
+        return loss, g1, g2
+
+    def train_step(self, X, T, lr, loss=None):
+        loss = torch.zeros(1, dtype=torch.float64, device=X.device) if loss is None else loss
+        _check(lib().bs_mlp_train_step(self.handle, X.shape[0], _fptr(X, "X"), _fptr(T, "T"),
+                                       float(lr), _ptr(loss), _stream()), "bs_mlp_train_step")
+        return loss
+
+
+def mlp_pairs(problem, r, elems, negate_odd=False, out=None):
+    """Training pairs (X, T) of the elements `elems` (int32 CUDA tensor) from a
+    residual r (CUDA float64 N_G vector): X = u / rms, T = (e_I - u_I) / rms
+    with e_I the element-interior error (bs_mlp_pairs)."""
+    L = _bind(["bs_mlp_pairs"])
+    Np = (problem.map.N + 1) ** 3
+    n = elems.numel()
+    if out is None:
+        X = torch.empty((n, Np), dtype=torch.float32, device=r.device)
+        T = torch.empty((n, Np), dtype=torch.float32, device=r.device)
+    else:
+        X, T = out
+    _check(L.bs_mlp_pairs(problem.handle, _ptr(r), n, _ptr(elems, torch.int32),
+                          int(bool(negate_odd)), _fptr(X), _fptr(T), _stream()), "bs_mlp_pairs")
+    return X, T
+
+
+def fpcg_learned(problem, mlp, b, x=None, tol=1e-8, maxit=100000, flags=0, check=True):
+    """Flexible PCG with the learned correction (mlp None: Jacobi only).
+    Returns (x, info dict)."""
+    L = _bind(["bs_fpcg_learned"])
+    x = torch.zeros_like(b) if x is None else x
+    info = CgInfo()
+    rc = L.bs_fpcg_learned(problem.handle, mlp.handle if mlp is not None else None, _ptr(b),
+                           _ptr(x), tol, maxit, flags, ctypes.byref(info), _stream())
+    if check and rc != BS_OK:
+        _check(rc, "bs_fpcg_learned")
+    d = info.as_dict()
+    d["rc"] = rc
+    return x, d

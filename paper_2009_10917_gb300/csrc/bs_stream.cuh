@@ -97,6 +97,8 @@ struct CgState {
   int maxit;      // stop after this many iterations
   int fixed;      // 1: ignore eps
   int done;       // 0 running; 1 converged; 2 breakdown; 3 iteration limit
+  int fallback;   // learned FPCG: 1 if this iteration's correction was rejected
+  int nfallback;  // learned FPCG: corrections rejected so far
   double *hist;   // optional [3*(maxit+1)] alpha, beta, rr per iteration
 };
 

@@ -460,7 +460,118 @@ def test_fpcg_with_exact_local_inverse_beats_jacobi():
     W1 = np.concatenate([np.eye(Np), -np.eye(Np)]).astype(np.float32)
     W2 = np.concatenate([Mlin, -Mlin], axis=1).astype(np.float32)
     b = synth.uniform(m.NG, 3)
-    _, it, _, fb = oracle.fpcg(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, W1, W2, bf16=False,
+    _, it, _, fb = oracle.fpcg(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, W1, W2, prec=oracle.PREC_FP64,
                                tol=1e-10, maxit=2000)
     _, itj, _ = oracle.pcg_jacobi(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, tol=1e-10, maxit=2000)
     assert it < itj and fb == 0
+
+
+def _interior_index(N):
+    Nq = N + 1
+    return np.array([i + Nq * (j + Nq * k) for k in range(1, N) for j in range(1, N)
+                     for i in range(1, N)], dtype=np.int64)
+
+
+def test_interior_pairs_match_dense_fem():
+    """T = (A_II^-1 r_I - D_I^-1 r_I) / rms from the independent dense
+    element matrices; X = D^-1 r / rms from the dense assembled diagonal."""
+    N, lam = 3, 1e-2
+    m = synth.Mesh(3, N, seed=5)
+    coef = synth.lognormal(m.E, 6)
+    r = synth.uniform(m.NG, 7)
+    elems = np.array([0, 13, 26, 5], np.int32)
+    X, T = oracle.interior_pairs(m.E, N, m.h, lam, m.ids, m.NG, r, elems, coef=coef)
+    A = fem_ref.assemble(m, lam, coef)
+    S, M = fem_ref.element_matrices(N, m.h)
+    I = _interior_index(N)
+    u = r / np.diag(A)
+    for q, e in enumerate(elems):
+        idx = m.ids[e * m.Np:(e + 1) * m.Np]
+        ue = u[idx]
+        rms = np.sqrt(np.mean(ue ** 2))
+        Ae = coef[e] * S + lam * M
+        eI = np.linalg.solve(Ae[np.ix_(I, I)], r[idx[I]])
+        want = np.zeros(m.Np)
+        want[I] = (eI - ue[I]) / rms
+        np.testing.assert_allclose(X[q], ue / rms, rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(T[q], want, rtol=1e-5, atol=1e-6 * np.abs(want).max())
+        # the interior block is the assembled matrix's (interior nodes have valence 1)
+        np.testing.assert_allclose(A[np.ix_(idx[I], idx[I])], Ae[np.ix_(I, I)], rtol=1e-12,
+                                   atol=1e-15)
+
+
+def test_interior_pairs_degree_two_and_signs():
+    """N = 2: one interior node, whose interior solve is its Jacobi step, so
+    T = 0; negate_odd flips every odd pair."""
+    m = synth.Mesh(2, 2, seed=3)
+    r = synth.uniform(m.NG, 4)
+    elems = np.arange(m.E, dtype=np.int32)
+    X, T = oracle.interior_pairs(m.E, 2, m.h, 1.0, m.ids, m.NG, r, elems)
+    assert np.abs(T).max() <= 1e-6 * np.abs(X).max()
+    Xs, Ts = oracle.interior_pairs(m.E, 2, m.h, 1.0, m.ids, m.NG, r, elems, negate_odd=True)
+    sgn = np.where(np.arange(m.E) % 2 == 0, 1.0, -1.0)[:, None]
+    assert np.array_equal(Xs, (X * sgn).astype(np.float32))
+    assert np.array_equal(Ts, (T * sgn).astype(np.float32))
+    # rms normalisation: every row of X has mean square 1
+    np.testing.assert_allclose(np.mean(X.astype(np.float64) ** 2, axis=1), 1.0, rtol=1e-6)
+
+
+def test_mlp_odd_part_is_half_w2_w1():
+    W1, W2 = _mlp(7, 10, 8)
+    X = synth.uniform(6 * 7, 9).reshape(6, 7).astype(np.float32)
+    y, _ = oracle.mlp_forward(W1, W2, X, odd=True)
+    want = 0.5 * (X.astype(np.float64) @ W1.T.astype(np.float64)) @ W2.T.astype(np.float64)
+    np.testing.assert_allclose(y, want, rtol=1e-12, atol=1e-13)
+    # odd and linear: f_odd(-x) = -f_odd(x), f_odd(2x) = 2 f_odd(x)
+    yn, _ = oracle.mlp_forward(W1, W2, -X, odd=True)
+    y2, _ = oracle.mlp_forward(W1, W2, 2 * X, odd=True)
+    assert np.array_equal(yn, -y) and np.array_equal(y2, 2 * y)
+    # and the full network is f_odd plus the even part W2 |W1 x| / 2
+    yf, _ = oracle.mlp_forward(W1, W2, X)
+    even = 0.5 * np.abs(X.astype(np.float64) @ W1.T.astype(np.float64)) @ W2.T.astype(np.float64)
+    np.testing.assert_allclose(yf, y + even, rtol=1e-12, atol=1e-13)
+
+
+def test_mlp_bf16x3_error_bound():
+    """Carrying every value as hi + lo bf16 leaves a relative error of order
+    2^-16 per product (the dropped lo*lo term and lo's own rounding), far
+    below plain bf16's 2^-8."""
+    D, H = 216, 256
+    W1 = (synth.uniform(H * D, 11, 0).reshape(H, D) * np.sqrt(3.0 / D)).astype(np.float32)
+    W2 = (synth.uniform(D * H, 11, 1).reshape(D, H) * np.sqrt(3.0 / H)).astype(np.float32)
+    X = synth.uniform(8 * D, 12).reshape(8, D).astype(np.float32)
+    y0, h0 = oracle.mlp_forward(W1, W2, X)
+    y3, _ = oracle.mlp_forward(W1, W2, X, prec=oracle.PREC_BF16X3)
+    y1, _ = oracle.mlp_forward(W1, W2, X, prec=oracle.PREC_BF16)
+    a1 = np.abs(W1.astype(np.float64))
+    a2 = np.abs(W2.astype(np.float64))
+    bound = 2.0 ** -14 * (a2 @ (a1 @ np.abs(X.astype(np.float64)).T)).T
+    assert np.all(np.abs(y3 - y0) <= bound)
+    assert np.linalg.norm(y3 - y0) <= 1e-2 * np.linalg.norm(y1 - y0)
+    # odd parts agree the same way
+    yo0, _ = oracle.mlp_forward(W1, W2, X, odd=True)
+    yo3, _ = oracle.mlp_forward(W1, W2, X, prec=oracle.PREC_BF16X3, odd=True)
+    assert np.all(np.abs(yo3 - yo0) <= bound)
+
+
+def test_fpcg_odd_part_equals_relu_pair_network():
+    """The linear correction M u written as ReLU pairs (W1 = [I; -I],
+    W2 = [M, -M]) and as an odd part (W1 = I, W2 = 2M) is the same
+    preconditioner, so FPCG takes the same steps."""
+    m = synth.Mesh(2, 2, seed=1)
+    S, Mm = fem_ref.element_matrices(2, m.h)
+    Ae = S + 1e-2 * Mm
+    Np = m.Np
+    Mlin = 0.5 * (np.eye(Np) - Ae / np.diag(Ae)[:, None])
+    b = synth.uniform(m.NG, 3)
+    W1p = np.concatenate([np.eye(Np), -np.eye(Np)]).astype(np.float32)
+    W2p = np.concatenate([Mlin, -Mlin], axis=1).astype(np.float32)
+    W1o = np.eye(Np, dtype=np.float32)
+    W2o = (2 * Mlin).astype(np.float32)
+    kw = dict(prec=oracle.PREC_FP64, tol=1e-10, maxit=2000)
+    xp, itp, rrp, _ = oracle.fpcg(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, W1p, W2p, **kw)
+    xo, ito, rro, _ = oracle.fpcg(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, W1o, W2o, odd=True, **kw)
+    assert abs(itp - ito) <= 1
+    # the two differ only by rounding order: same early history, same answer
+    np.testing.assert_allclose(rro[:10], rrp[:10], rtol=1e-9)
+    assert np.linalg.norm(xo - xp) <= 1e-8 * np.linalg.norm(xp)
