@@ -266,7 +266,8 @@ typedef struct bs_mlp bs_mlp;
 enum {
   BS_MLP_BF16X3 = 1, /* bs_mlp_create: hi + lo bf16 operands (three products) */
   BS_MLP_ODD = 2,    /* bs_mlp_forward: the odd part W2 W1 x / 2              */
-  BS_FPCG_ODD = 64   /* bs_fpcg_learned: precondition with the odd part       */
+  BS_FPCG_ODD = 64,       /* bs_fpcg_learned: precondition with the odd part  */
+  BS_FPCG_NO_JUDGE = 128  /* bs_fpcg_learned: never switch to Jacobi for good */
 };
 
 /* Create a network from HOST weights h_W1 [H x D], h_W2 [D x H] (copied).
@@ -311,18 +312,24 @@ int bs_mlp_pairs(const bs_problem *prob, const double *d_r, int64_t count,
                  void *stream);
 
 /* Flexible PCG with the learned correction, x0 = 0:
- *   z = M(r) = D^-1 r + v^-1 Z^T y,  y_e = rms_e g(Z D^-1 r / rms_e)_e
- * with g = f, or its odd part with BS_FPCG_ODD, v the node valences;
+ *   z = M(r) = D^-1 r + corr,  corr_g = rms_e g(u_e / rms_e)_l at each
+ *   element-interior node g (local index l of element e, 1 <= i,j,k <= N-1),
+ *   0 at every other node, u = Z D^-1 r, rms_e = sqrt(mean u_e^2),
+ * with g = f, or its odd part with BS_FPCG_ODD.  The training targets (the
+ * element-interior error of bs_mlp_pairs) vanish off the interior, so only
+ * interior outputs are used; each interior node belongs to one element.
  * alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap; beta = r.(z' - z) /
  * (r.z)_old (Polak-Ribiere); p = z' + beta p.  mlp == NULL gives Jacobi-PCG.
  * Jacobi is the fallback and the judge: an iteration whose r.z' <= 0 (or not
  * finite) uses z' = D^-1 r (counted in info->fallbacks), and if r.r has not
- * fallen by 4 within 256 iterations the solve restarts from the current x
+ * fallen by 4 within max(1024, 16 N_G^(1/3)) iterations (a stall guard: r.r
+ * is not monotone, and Jacobi-PCG itself has gone 7.5 N_G^(1/3) iterations
+ * without halving it on these operators) the solve restarts from the current x
  * with Jacobi for good (info->outer = the iteration of that switch, 0 if
  * none).  Stop: r.r <= tol^2 b.b or maxit.  flags: BS_CG_GRAPH,
- * BS_FPCG_ODD.  The network's input size must be (N+1)^3.  Synchronises
- * `stream`.  Returns BS_ERR_NOT_CONVERGED or BS_ERR_BREAKDOWN as
- * bs_cg_solve does. */
+ * BS_FPCG_ODD, BS_FPCG_NO_JUDGE.  The network's input size must be (N+1)^3,
+ * 2 <= N <= 9.  Synchronises `stream`.  Returns BS_ERR_NOT_CONVERGED or
+ * BS_ERR_BREAKDOWN as bs_cg_solve does. */
 int bs_fpcg_learned(const bs_problem *prob, bs_mlp *mlp, const double *b, double *x,
                     double tol, int32_t maxit, int32_t flags, bs_cg_info *info,
                     void *stream);

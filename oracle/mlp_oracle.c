@@ -27,7 +27,10 @@
  *         w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), in float.
  *   Preconditioner: u = Z (D^-1 r); per element rms_e = sqrt(mean u_e^2);
  *         y_e = rms_e MLP(u_e / rms_e) (0 where rms_e = 0), MLP = f or f_odd;
- *         z = D^-1 r + v^-1 (Z^T y), v the valence of each global node.
+ *         z = D^-1 r + corr, corr_g = y_e at the element-interior node g of
+ *         element e (1 <= i,j,k <= N-1; one element per interior node), 0 at
+ *         every other node: the training targets (the element-interior
+ *         error) vanish there, so those outputs are not used.
  *   FPCG: alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap;
  *         z' = M(r); if r.z' <= 0 or not finite, z' = D^-1 r;
  *         beta = r.(z' - z) / (r_old.z_old); p = z' + beta p.
@@ -173,9 +176,10 @@ int bso_diag_A(int E, int N, double h, double lambda, const double *coef,
                const int32_t *ids, int64_t NG, double *diag);
 
 /* z = D^-1 r + v^-1 Z^T (rms MLP(Z D^-1 r / rms)); W2 == NULL: z = D^-1 r. */
-static void precond(int E, int Np, const int32_t *ids, int64_t NG, const double *dg,
-                    const double *val, const float *W1, const float *W2, int H, int prec,
-                    int odd, const double *r, double *z) {
+static void precond(int E, int N, const int32_t *ids, int64_t NG, const double *dg,
+                    const float *W1, const float *W2, int H, int prec, int odd,
+                    const double *r, double *z) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
   for (int64_t g = 0; g < NG; ++g) z[g] = r[g] / dg[g];
   if (!W2) return;
   float *x = malloc(sizeof(float) * Np);
@@ -192,10 +196,15 @@ static void precond(int E, int Np, const int32_t *ids, int64_t NG, const double 
     if (!(rms > 0.0)) continue;
     for (int l = 0; l < Np; ++l) x[l] = (float)((id[l] >= 0 ? z[id[l]] : 0.0) / rms);
     bso_mlp_forward(1, Np, H, W1, W2, x, y, NULL, prec, odd);
-    for (int l = 0; l < Np; ++l)
-      if (id[l] >= 0) corr[id[l]] += rms * y[l];
+    /* element-interior outputs only; each interior node has one element */
+    for (int k = 1; k < N; ++k)
+      for (int j = 1; j < N; ++j)
+        for (int i = 1; i < N; ++i) {
+          const int l = i + Nq * (j + Nq * k);
+          if (id[l] >= 0) corr[id[l]] += rms * y[l];
+        }
   }
-  for (int64_t g = 0; g < NG; ++g) z[g] += val[g] > 0 ? corr[g] / val[g] : 0.0;
+  for (int64_t g = 0; g < NG; ++g) z[g] += corr[g];
   free(x); free(y); free(corr);
 }
 
@@ -209,21 +218,16 @@ static double dot(int64_t n, const double *a, const double *b) {
  * counts iterations whose correction was rejected. */
 int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const int32_t *ids,
              int64_t NG, const float *W1, const float *W2, int H, int prec, int odd,
-             const double *b,
-             double *x, double tol, int maxit, double *hist_rr, int *fallbacks) {
-  const int Np = (N + 1) * (N + 1) * (N + 1);
-  double *buf = malloc(sizeof(double) * 7 * NG);
+             const double *b, double *x, double tol, int maxit, double *hist_rr,
+             int *fallbacks) {
+  double *buf = malloc(sizeof(double) * 6 * NG);
   if (!buf) return -2;
-  double *r = buf, *p = r + NG, *Ap = p + NG, *z = Ap + NG, *zn = z + NG, *dg = zn + NG,
-         *val = dg + NG;
+  double *r = buf, *p = r + NG, *Ap = p + NG, *z = Ap + NG, *zn = z + NG, *dg = zn + NG;
   bso_diag_A(E, N, h, lambda, coef, ids, NG, dg);
-  for (int64_t g = 0; g < NG; ++g) val[g] = 0.0;
-  for (int64_t l = 0; l < (int64_t)E * Np; ++l)
-    if (ids[l] >= 0) val[ids[l]] += 1.0;
   for (int64_t g = 0; g < NG; ++g) x[g] = 0.0;
   for (int64_t g = 0; g < NG; ++g) r[g] = b[g];
   int fb = 0;
-  precond(E, Np, ids, NG, dg, val, W1, W2, H, prec, odd, r, z);
+  precond(E, N, ids, NG, dg, W1, W2, H, prec, odd, r, z);
   double rz = dot(NG, r, z);
   if (!(rz > 0.0) || !isfinite(rz)) {
     for (int64_t g = 0; g < NG; ++g) z[g] = r[g] / dg[g];
@@ -248,7 +252,7 @@ int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const in
     ++j;
     if (hist_rr) hist_rr[j] = rr;
     if (rr <= eps) break;
-    precond(E, Np, ids, NG, dg, val, W1, W2, H, prec, odd, r, zn);
+    precond(E, N, ids, NG, dg, W1, W2, H, prec, odd, r, zn);
     double rzn = dot(NG, r, zn);
     if (!(rzn > 0.0) || !isfinite(rzn)) {
       for (int64_t g = 0; g < NG; ++g) zn[g] = r[g] / dg[g];

@@ -36,6 +36,7 @@ BS_CG_REFINED_F32 = 32
 BS_MLP_BF16X3 = 1
 BS_MLP_ODD = 2
 BS_FPCG_ODD = 64
+BS_FPCG_NO_JUDGE = 128
 
 
 class BSError(RuntimeError):

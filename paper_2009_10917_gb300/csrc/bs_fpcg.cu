@@ -3,14 +3,22 @@
 //
 // Preconditioner (no counterpart in the paper):
 //   u = Z (D^-1 r);  rms_e = sqrt(mean of u_e^2);  X_e = u_e / rms_e
-//   Y = W2 relu(W1 X), or the odd part W2 W1 X / 2 (two tensor-core GEMMs
-//       over all elements at once, in the network's BF16 or BF16x3 mode)
-//   z = D^-1 r + v^-1 Z^T (rms_e Y_e)        (v: valence of each global node)
-// Flexible CG (Polak-Ribiere): alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap;
-// z' = M(r), replaced by D^-1 r when r.z' <= 0 or not finite (the Jacobi
-// fallback); beta = r.(z' - z) / (r.z)_old; p = z' + beta p.  Every scalar
-// and the fallback decision are formed on the device; an iteration is nine
-// launches and never waits for the host.
+//   Y = W2 relu(W1 X), or the odd part W2 W1 X / 2, at the element-interior
+//       outputs only (tensor-core GEMMs over all elements at once, in the
+//       network's BF16 or BF16x3 mode; the odd part is one GEMM with
+//       L = W2 W1 / 2)
+//   z = D^-1 r + corr, corr_g = rms_e Y_e,l at the interior node g of element
+//       e (local index l), 0 elsewhere
+// The training targets are the element-interior error, zero at every other
+// node, so only interior outputs are used; interior nodes belong to one
+// element each, so the GEMM epilogue writes them straight into corr (no
+// gather).  Flexible CG (Polak-Ribiere): alpha = r.z / p.Ap; x += alpha p;
+// r -= alpha Ap; z' = M(r), replaced by D^-1 r when r.z' <= 0 or not finite
+// (the Jacobi fallback); beta = r.(z' - z) / (r.z)_old; p = z' + beta p.
+// Every scalar and the fallback decision are formed on the device; an
+// iteration is seven launches (six for Jacobi-only) and never waits for the
+// host.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -23,43 +31,58 @@ constexpr int kPrepBlock = 256;  // 8 warps, one element per warp
 
 // One warp per element: u = D^-1 r through the map, rms, the X row as the
 // GEMM operand ([hi] or [hi | hi | lo], padding zero), and rms * oscale to
-// rmsv[e] (0 for an all-zero element).
+// rmsv[e] (0 for an all-zero element).  GB300's FP64 pipe (and the
+// conversions, which share it) runs at 1/64 of the FP32 rate, so each node
+// costs one DMUL (u) and one conversion; the sum of squares and the scaling
+// are FP32.  rms is only a normalisation: the network's output is multiplied
+// back by the same value, so its rounding does not matter.
+constexpr int kPrepMaxPerLane = 32;  // (N+1)^3 <= 1024 nodes per element
+// Row q of X and rmsv belongs to element order[q]: elements visited in the
+// map's order (sorted by smallest global index) meet their neighbours' reads
+// of r and D^-1 in L2, where the random element numbering would not.
 __global__ void __launch_bounds__(kPrepBlock)
     k_fp_prep(int64_t E, int Np, int Dp, int split, float oscale,
-              const int32_t *__restrict__ ids, const double *__restrict__ r,
-              const double *__restrict__ dinv, __nv_bfloat16 *__restrict__ X,
-              float *__restrict__ rmsv, const CgState *st) {
+              const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
+              const double *__restrict__ r, const double *__restrict__ dinv,
+              __nv_bfloat16 *__restrict__ X, float *__restrict__ rmsv, const CgState *st) {
   if (cg_halted(st)) return;
   const int lane = threadIdx.x & 31;
-  const int64_t e = (int64_t)blockIdx.x * (kPrepBlock / 32) + (threadIdx.x >> 5);
-  if (e >= E) return;
+  const int64_t q = (int64_t)blockIdx.x * (kPrepBlock / 32) + (threadIdx.x >> 5);
+  if (q >= E) return;
+  const int64_t e = order[q];
   const int32_t *id = ids + e * Np;
-  double ss = 0.0;
-  for (int l = lane; l < Np; l += 32) {
-    const int32_t g = id[l];
-    const double u = g >= 0 ? dinv[g] * r[g] : 0.0;
-    ss = fma(u, u, ss);
-  }
+  float uf[kPrepMaxPerLane];
+  float ss = 0.f;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
-  const double rms = sqrt(ss / Np);
-  const double inv = rms > 0.0 ? 1.0 / rms : 0.0;
-  __nv_bfloat16 *row = X + e * (split ? 3 * Dp : Dp);
-  for (int l = lane; l < Dp; l += 32) {
+  for (int t = 0; t < kPrepMaxPerLane; ++t) {
+    const int l = lane + 32 * t;
     float v = 0.f;
     if (l < Np) {
-      const int32_t g = id[l];
-      v = g >= 0 ? (float)(dinv[g] * r[g] * inv) : 0.f;
+      const int32_t g = __ldcs(id + l);
+      v = g >= 0 ? (float)(__ldg(dinv + g) * __ldg(r + g)) : 0.f;
     }
+    uf[t] = v;
+    ss = fmaf(v, v, ss);
+    if (32 * (t + 1) >= Np) break;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  const float rms = sqrtf(ss / (float)Np);
+  const float inv = rms > 0.f ? 1.0f / rms : 0.f;
+  __nv_bfloat16 *row = X + q * (split ? 3 * Dp : Dp);
+#pragma unroll
+  for (int t = 0; t < kPrepMaxPerLane; ++t) {
+    const int l = lane + 32 * t;
+    if (l >= Dp) break;
     __nv_bfloat16 hi, lo;
-    bf16_split(v, hi, lo);
+    bf16_split(l < Np ? uf[t] * inv : 0.f, hi, lo);
     row[l] = hi;
     if (split) {
       row[Dp + l] = hi;
       row[2 * Dp + l] = lo;
     }
   }
-  if (lane == 0) rmsv[e] = (float)rms * oscale;
+  if (lane == 0) rmsv[q] = rms * oscale;
 }
 
 // Three-value last-block-done combine (partials holds 3 * gridDim.x).
@@ -116,68 +139,29 @@ __device__ void fpcg_scalars(CgState *st, double rzn, double rzo, double rzj, in
   st->rz = rzn;
 }
 
-// Gather the correction and form z' = D^-1 r + v^-1 (Z^T yL) with the three
-// dot products; z holds the old z on entry and z' on exit.
-__global__ void __launch_bounds__(kGatherBlock)
-    k_gather_fpcg(int64_t ntiles, const int2 *__restrict__ tiles,
-                  const int32_t *__restrict__ row_starts, const int32_t *__restrict__ col_ids,
-                  const double *__restrict__ yL, const double *__restrict__ r,
-                  const double *__restrict__ dinv, const double *__restrict__ vinv,
-                  double *__restrict__ z, double *partials, unsigned int *counter, CgState *st,
-                  int init, int have_mlp, int64_t NG) {
-  __shared__ double s_v[kTileNnz];
+// z' = D^-1 r + corr (have_mlp) or D^-1 r, with the three dot products
+// r.z', r.z_old, r.(D^-1 r); z holds the old z on entry and z' on exit.
+__global__ void __launch_bounds__(kReduceBlock)
+    k_fpcg_z(int64_t NG, const double *__restrict__ r, const double *__restrict__ dinv,
+             const double *__restrict__ corr, double *__restrict__ z, double *partials,
+             unsigned int *counter, CgState *st, int init, int have_mlp) {
   if (cg_halted(st)) return;
   double an = 0.0, ao = 0.0, aj = 0.0;
-  auto row_op = [&](int64_t g, double s) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = tid; g < NG; g += nth) {
     const double rg = r[g], zj = dinv[g] * rg;
-    const double zn = have_mlp ? fma(vinv[g], s, zj) : zj;
+    const double zn = have_mlp ? zj + corr[g] : zj;
     if (!init) ao = fma(rg, z[g], ao);
     an = fma(rg, zn, an);
     aj = fma(rg, zj, aj);
     z[g] = zn;
-  };
-  if (have_mlp) {
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int2 lo = tiles[t], hi = tiles[t + 1];
-      const int32_t r0 = lo.x, r1 = hi.x, k0 = lo.y, nk = hi.y - lo.y;
-      if (nk <= kTileNnz) {
-        constexpr int U = kTileNnz / kGatherBlock;
-        int32_t c[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int kk = threadIdx.x + u * kGatherBlock;
-          c[u] = kk < nk ? col_ids[k0 + kk] : -1;
-        }
-        double v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = c[u] >= 0 ? __ldcs(yL + c[u]) : 0.0;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int kk = threadIdx.x + u * kGatherBlock;
-          if (kk < nk) s_v[kk] = v[u];
-        }
-        __syncthreads();
-        for (int32_t g = r0 + threadIdx.x; g < r1; g += kGatherBlock)
-          row_op(g, row_sum(s_v, row_starts[g] - k0, row_starts[g + 1] - k0));
-        __syncthreads();
-      } else {
-        for (int32_t g = r0 + threadIdx.x; g < r1; g += kGatherBlock) {
-          double s = 0.0;
-          for (int32_t k = row_starts[g]; k < row_starts[g + 1]; ++k) s = s + yL[col_ids[k]];
-          row_op(g, s);
-        }
-      }
-    }
-  } else {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < NG;
-         g += (int64_t)gridDim.x * blockDim.x)
-      row_op(g, 0.0);
   }
-  const double pn = block_sum<kGatherBlock>(an);
-  const double po = block_sum<kGatherBlock>(ao);
-  const double pj = block_sum<kGatherBlock>(aj);
+  const double pn = block_sum<kReduceBlock>(an);
+  const double po = block_sum<kReduceBlock>(ao);
+  const double pj = block_sum<kReduceBlock>(aj);
   double tn, to, tj;
-  if (grid_combine3<kGatherBlock>(pn, po, pj, partials, counter, &tn, &to, &tj) &&
+  if (grid_combine3<kReduceBlock>(pn, po, pj, partials, counter, &tn, &to, &tj) &&
       threadIdx.x == 0)
     fpcg_scalars(st, tn, to, tj, init);
 }
@@ -250,16 +234,6 @@ __global__ void k_fpcg_init(CgState *st, double tol2, int maxit) {
   st->done = !isfinite(st->bb) ? 2 : (st->bb <= st->eps ? 1 : (maxit <= 0 ? 3 : 0));
 }
 
-__global__ void k_fill_vinv(int64_t NG, const int32_t *__restrict__ row_starts,
-                            double *__restrict__ vinv) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = tid; g < NG; g += nth) {
-    const int v = row_starts[g + 1] - row_starts[g];
-    vinv[g] = v > 0 ? 1.0 / v : 0.0;
-  }
-}
-
 __global__ void k_recip(int64_t n, const double *__restrict__ d, double *__restrict__ inv) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -267,7 +241,7 @@ __global__ void k_recip(int64_t n, const double *__restrict__ d, double *__restr
 }
 
 struct FpVecs {
-  double *r, *p, *Ap, *z, *dinv, *vinv;
+  double *r, *p, *Ap, *z, *dinv, *corr;
 };
 static FpVecs fpvecs(const bs_problem *P) {
   const int64_t s = P->map->NG + 2;
@@ -284,27 +258,62 @@ static int precondition(const bs_problem *P, bs_mlp *mlp, int odd, int init, cud
   if (mlp) {
     const int64_t E = m->E;
     float *rmsv = mlp->Y;  // E floats of inference scratch
-    // the odd part W2 W1 x / 2: identity hidden activation, output scale 1/2
-    k_fp_prep<<<(unsigned)((E + 7) / 8), kPrepBlock, 0, s>>>(E, Np, mlp->Dp, mlp->split,
-                                                            odd ? 0.5f : 1.0f, m->d_ids, v.r,
+    k_fp_prep<<<(unsigned)((E + 7) / 8), kPrepBlock, 0, s>>>(E, Np, mlp->Dp, mlp->split, 1.0f,
+                                                            m->d_elem_order, m->d_ids, v.r,
                                                             v.dinv, mlp->Xb, rmsv, st);
     BS_LAUNCH_CHECK();
     GemmArgs b{};
-    b.ldc = Np;
-    b.nvalid = Np;
-    b.out_f64 = P->d_ApL;
+    b.nvalid = mlp->nI;
+    b.out_f64 = v.corr;
     b.scale = rmsv;
+    b.ids = m->d_ids;
+    b.order = m->d_elem_order;
+    b.lidx = mlp->lidx;
+    b.np = Np;
     b.st = st;
-    if (int rc = mlp_forward_packed(mlp, E, odd ? 0 : 1, b, EPI_SCALE_F64, s)) return rc;
+    if (odd) {
+      // the odd part W2 W1 x / 2 is linear: one GEMM with the interior rows of
+      // L = W2 W1 / 2
+      const int K1 = mlp->split ? 3 * mlp->Dp : mlp->Dp;
+      b.A = mlp->Xb;
+      b.B = mlp->Wint;
+      b.M = E;
+      b.N = mlp->nI;
+      b.K = K1;
+      b.lda = K1;
+      b.ldb = K1;
+      if (int rc = launch_gemm(EPI_SCATTER_F64, b, s)) return rc;
+    } else {
+      // hidden layer over all H units, then the interior rows of W2
+      const int K1 = mlp->split ? 3 * mlp->Dp : mlp->Dp, K2 = mlp->split ? 3 * mlp->H : mlp->H;
+      GemmArgs a{};
+      a.A = mlp->Xb;
+      a.B = mlp->W1b;
+      a.M = E;
+      a.N = mlp->H;
+      a.K = K1;
+      a.lda = K1;
+      a.ldb = K1;
+      a.ldc = K2;
+      a.out_b16 = mlp->Hb;
+      a.relu = 1;
+      a.split = mlp->split ? mlp->H : 0;
+      a.st = st;
+      if (int rc = launch_gemm(EPI_HIDDEN, a, s)) return rc;
+      b.A = mlp->Hb;
+      b.B = mlp->Wint;
+      b.M = E;
+      b.N = mlp->nI;
+      b.K = K2;
+      b.lda = K2;
+      b.ldb = K2;
+      if (int rc = launch_gemm(EPI_SCATTER_F64, b, s)) return rc;
+    }
   }
-  const int grid_cap = kMaxPartials / 3;
-  int grid = mlp ? stream_grid(m->ntiles, 1, 1, blocks_per_sm(k_gather_fpcg, kGatherBlock))
-                 : stream_grid(m->NG, 1, kGatherBlock, 4);
-  if (grid > grid_cap) grid = grid_cap;
-  k_gather_fpcg<<<grid, kGatherBlock, 0, s>>>(m->ntiles, m->d_tiles, m->d_row_starts,
-                                              m->d_col_ids, P->d_ApL, v.r, v.dinv, v.vinv, v.z,
-                                              P->d_partials, P->d_counter, st, init,
-                                              mlp ? 1 : 0, m->NG);
+  int grid = stream_grid(m->NG, 1, kReduceBlock, blocks_per_sm(k_fpcg_z, kReduceBlock));
+  if (grid > kMaxPartials / 3) grid = kMaxPartials / 3;
+  k_fpcg_z<<<grid, kReduceBlock, 0, s>>>(m->NG, v.r, v.dinv, v.corr, v.z, P->d_partials,
+                                         P->d_counter, st, init, mlp ? 1 : 0);
   BS_LAUNCH_CHECK();
   return BS_OK;
 }
@@ -477,8 +486,9 @@ static int fpcg_setup(const bs_problem *P, cudaStream_t s) {
   if (int rc = bs_diag_A(P, v.Ap, s)) return rc;
   const int grid = stream_grid(m->NG, 1, 256, 8);
   k_recip<<<grid, 256, 0, s>>>(m->NG, v.Ap, v.dinv);
-  k_fill_vinv<<<grid, 256, 0, s>>>(m->NG, m->d_row_starts, v.vinv);
   BS_LAUNCH_CHECK();
+  // corr is written only at element-interior nodes; the rest stays zero
+  BS_CUDA_TRY(cudaMemsetAsync(v.corr, 0, sizeof(double) * m->NG, s));
   return BS_OK;
 }
 
@@ -535,15 +545,19 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
   BS_CUDA_TRY(cudaGetDevice(&dev));
   BS_ARG(dev == P->device, "bs_fpcg_learned: problem on another device");
   BS_ARG(maxit >= 0 && tol >= 0.0 && std::isfinite(tol), "bs_fpcg_learned: bad tol or maxit");
-  BS_ARG((flags & ~(BS_CG_GRAPH | BS_FPCG_ODD)) == 0, "bs_fpcg_learned: unknown flags 0x%x",
-         (unsigned)flags);
+  BS_ARG((flags & ~(BS_CG_GRAPH | BS_FPCG_ODD | BS_FPCG_NO_JUDGE)) == 0,
+         "bs_fpcg_learned: unknown flags 0x%x", (unsigned)flags);
+  const bool judge = !(flags & BS_FPCG_NO_JUDGE);
   const int odd = (flags & BS_FPCG_ODD) ? 1 : 0;
   const bs_map *m = P->map;
   const int Np = (P->N + 1) * (P->N + 1) * (P->N + 1);
   if (mlp) {
     BS_ARG(mlp->device == dev, "bs_fpcg_learned: mlp on another device");
     BS_ARG(mlp->D == Np, "bs_fpcg_learned: mlp input size %d != (N+1)^3 = %d", mlp->D, Np);
+    BS_ARG(Np <= 32 * kPrepMaxPerLane, "bs_fpcg_learned: degree %d above 9", P->N);
     if (int rc = mlp_ensure(mlp, m->E > 32 ? m->E : 32)) return rc;
+    BS_ARG(mlp->nI > 0, "bs_fpcg_learned: the network needs N >= 2 (element-interior outputs)");
+    if (int rc = mlp_interior_operand(mlp, odd, as_stream(stream))) return rc;
   }
   BS_ARG(m->NG == 0 || (b && x), "bs_fpcg_learned: NULL vector");
   cudaStream_t s = as_stream(stream);
@@ -588,8 +602,12 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
   if (graph && (rc = capture(mlp))) return rc;
   // Jacobi judges the learned correction: if the residual has not halved
   // within kStall iterations, the solve restarts from the current iterate
-  // with the Jacobi preconditioner (z = D^-1 r, p = z) for good.
-  constexpr int kStall = 256;
+  // with the Jacobi preconditioner (z = D^-1 r, p = z) for good.  r.r is not
+  // monotone in (F)CG: on these operators Jacobi-PCG itself has gone up to
+  // about 7.5 N_G^(1/3) iterations without halving it, so the window is
+  // 16 N_G^(1/3) (at least 1024) -- a guard against a correction that stalls
+  // the solve, not a race against Jacobi.
+  const int kStall = std::max(1024, (int)(16.0 * std::cbrt((double)m->NG)));
   bs_mlp *net = mlp;
   int switched_at = 0, window_iter = 0;
   double window_rr = INFINITY;
@@ -607,7 +625,7 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
     }
     const CgState &h = *P->h_state;
     if (h.done) break;
-    if (net) {
+    if (net && judge) {
       if (h.rr <= 0.25 * window_rr) {  // r.r down by 4: the residual has halved
         window_rr = h.rr;
         window_iter = h.iter;

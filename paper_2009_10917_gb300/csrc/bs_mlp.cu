@@ -9,7 +9,7 @@
 
 namespace bs {
 
-constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8;
+constexpr int GBM = 128, GBK = 32, GPAD = 8;
 constexpr int GTHREADS = 256;
 
 __device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, int bytes) {
@@ -35,32 +35,40 @@ __device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// C = A B^T on one 128 x 128 tile per block; 8 warps as 2 (M) x 4 (N), each
-// warp 64 x 32 = 4 x 4 mma tiles of 16 x 8.
-template <int EPI>
+// C = A B^T on one 128 x BN tile per block (BN = 128 or 64); 8 warps as
+// 2 (M) x 4 (N) warps of 64 x 32 for BN = 128, 4 x 2 warps of 32 x 32 for
+// BN = 64 (outputs narrower than 64, as the 64 element-interior outputs of a
+// degree-5 element, would waste half of a 128-wide tile).
+template <int EPI, int BN>
 __global__ void __launch_bounds__(GTHREADS) k_gemm_tn(GemmArgs g) {
+  constexpr int WM = BN == 128 ? 2 : 4, WN = 8 / WM;
+  constexpr int TM = GBM / WM, TN = BN / WN, MT = TM / 16, NT = TN / 8;
+  static_assert(NT % 2 == 0 && MT >= 1, "warp tile");
   __shared__ __align__(16) __nv_bfloat16 sA[2][GBM][GBK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 sB[2][GBN][GBK + GPAD];
+  __shared__ __align__(16) __nv_bfloat16 sB[2][BN][GBK + GPAD];
   if (cg_halted(g.st)) return;
   const int64_t m0 = (int64_t)blockIdx.y * GBM;
-  const int n0 = blockIdx.x * GBN;
+  const int n0 = blockIdx.x * BN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp >> 2, wn = warp & 3;
-  float acc[4][4][4];
+  const int wm = warp / WN, wn = warp % WN;
+  float acc[MT][NT][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NT; ++j)
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
   auto load = [&](int stage, int k0) {
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int c = tid + i * GTHREADS;
+    for (int c = tid; c < GBM * 4; c += GTHREADS) {
       const int row = c >> 2, col = (c & 3) * 8;
       const int64_t gm = m0 + row;
       const bool okA = gm < g.M;
       cp_async16_zfill(&sA[stage][row][col], g.A + (okA ? gm : 0) * g.lda + k0 + col, okA ? 16 : 0);
+    }
+#pragma unroll
+    for (int c = tid; c < BN * 4; c += GTHREADS) {
+      const int row = c >> 2, col = (c & 3) * 8;
       const int gn = n0 + row;
       const bool okB = gn < g.N;
       cp_async16_zfill(&sB[stage][row][col], g.B + (int64_t)(okB ? gn : 0) * g.ldb + k0 + col,
@@ -78,14 +86,14 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_tn(GemmArgs g) {
     const int st = kt & 1;
 #pragma unroll
     for (int kk = 0; kk < GBK; kk += 16) {
-      uint32_t af[4][4], bfr[4][2];
+      uint32_t af[MT][4], bfr[NT][2];
 #pragma unroll
-      for (int mt = 0; mt < 4; ++mt)
-        ldmatrix_x4(af[mt], &sA[st][wm * 64 + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+      for (int mt = 0; mt < MT; ++mt)
+        ldmatrix_x4(af[mt], &sA[st][wm * TM + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
 #pragma unroll
-      for (int np = 0; np < 2; ++np) {
+      for (int np = 0; np < NT / 2; ++np) {
         uint32_t r[4];
-        ldmatrix_x4(r, &sB[st][wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3)]
+        ldmatrix_x4(r, &sB[st][wn * TN + np * 16 + (lane & 7) + ((lane >> 4) << 3)]
                          [kk + ((lane >> 3) & 1) * 8]);
         bfr[2 * np][0] = r[0];
         bfr[2 * np][1] = r[1];
@@ -93,22 +101,24 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_tn(GemmArgs g) {
         bfr[2 * np + 1][1] = r[3];
       }
 #pragma unroll
-      for (int mt = 0; mt < 4; ++mt)
+      for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt]);
+        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt]);
     }
     __syncthreads();
   }
   const int gq = lane >> 2, tq = lane & 3;
 #pragma unroll
-  for (int mt = 0; mt < 4; ++mt)
+  for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
+    for (int h = 0; h < 2; ++h) {
+      const int64_t m = m0 + wm * TM + mt * 16 + gq + 8 * h;
+      if (m >= g.M) continue;
+      const int32_t *idrow = nullptr;
+      if (EPI == EPI_SCATTER_F64) idrow = g.ids + (int64_t)(g.order ? g.order[m] : m) * g.np;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t m = m0 + wm * 64 + mt * 16 + gq + 8 * h;
-        const int n = n0 + wn * 32 + nt * 8 + 2 * tq;
-        if (m >= g.M) continue;
+      for (int nt = 0; nt < NT; ++nt) {
+        const int n = n0 + wn * TN + nt * 8 + 2 * tq;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if (n + e >= g.N) continue;
@@ -128,11 +138,26 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_tn(GemmArgs g) {
             g.out_b16[o] = __bfloat162float(g.mask[m * g.ldmask + n + e]) > 0.f
                                ? __float2bfloat16_rn(v)
                                : __float2bfloat16_rn(0.f);
-          } else {
+          } else if (EPI == EPI_SCALE_F64) {
             if (n + e < g.nvalid) g.out_f64[o] = (double)v * (double)g.scale[m];
+          } else {
+            if (n + e < g.nvalid) {
+              const int32_t gid = idrow[g.lidx[n + e]];
+              if (gid >= 0) g.out_f64[gid] = (double)v * (double)g.scale[m];
+            }
           }
         }
       }
+    }
+}
+
+template <int EPI>
+static void launch_epi(const GemmArgs &a, int64_t gy, cudaStream_t s) {
+  if (a.N <= 64) {
+    k_gemm_tn<EPI, 64><<<dim3((unsigned)((a.N + 63) / 64), (unsigned)gy), GTHREADS, 0, s>>>(a);
+  } else {
+    k_gemm_tn<EPI, 128><<<dim3((unsigned)((a.N + 127) / 128), (unsigned)gy), GTHREADS, 0, s>>>(a);
+  }
 }
 
 int launch_gemm(int epi, const GemmArgs &a, cudaStream_t s) {
@@ -140,12 +165,12 @@ int launch_gemm(int epi, const GemmArgs &a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return BS_OK;
   const int64_t gy = (a.M + GBM - 1) / GBM;
   if (gy > 65535) return fail(BS_ERR_ARG, "gemm: M too large");
-  dim3 grid((unsigned)((a.N + GBN - 1) / GBN), (unsigned)gy);
   switch (epi) {
-    case EPI_F32: k_gemm_tn<EPI_F32><<<grid, GTHREADS, 0, s>>>(a); break;
-    case EPI_HIDDEN: k_gemm_tn<EPI_HIDDEN><<<grid, GTHREADS, 0, s>>>(a); break;
-    case EPI_MASK_BF16: k_gemm_tn<EPI_MASK_BF16><<<grid, GTHREADS, 0, s>>>(a); break;
-    case EPI_SCALE_F64: k_gemm_tn<EPI_SCALE_F64><<<grid, GTHREADS, 0, s>>>(a); break;
+    case EPI_F32: launch_epi<EPI_F32>(a, gy, s); break;
+    case EPI_HIDDEN: launch_epi<EPI_HIDDEN>(a, gy, s); break;
+    case EPI_MASK_BF16: launch_epi<EPI_MASK_BF16>(a, gy, s); break;
+    case EPI_SCALE_F64: launch_epi<EPI_SCALE_F64>(a, gy, s); break;
+    case EPI_SCATTER_F64: launch_epi<EPI_SCATTER_F64>(a, gy, s); break;
     default: return fail(BS_ERR_ARG, "gemm: unknown epilogue");
   }
   BS_LAUNCH_CHECK();
@@ -296,6 +321,66 @@ __global__ void k_unpad_cols(int R, int C, int ldp, const float *__restrict__ in
   }
 }
 
+// L [Dp x Dp] = W2 W1 / 2 (sums in FP64, rounded once to float; padded
+// rows and columns are zero because the masters' padding is) and its weight
+// operand Lb rows [hi] or [hi | lo | hi].
+__global__ void k_odd_matrix(int H, int Dp, int split, const float *__restrict__ W1,
+                             const float *__restrict__ W2, float *__restrict__ L,
+                             __nv_bfloat16 *__restrict__ Lb) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n = (int64_t)Dp * Dp, K1 = split ? 3 * Dp : Dp;
+  for (int64_t i = tid; i < n; i += nth) {
+    const int64_t r = i / Dp, c = i - r * Dp;
+    double acc = 0.0;
+    for (int j = 0; j < H; ++j) acc = fma((double)W2[r * H + j], (double)W1[(int64_t)j * Dp + c], acc);
+    const float v = (float)(0.5 * acc);
+    L[i] = v;
+    __nv_bfloat16 hi, lo;
+    bf16_split(v, hi, lo);
+    Lb[r * K1 + c] = hi;
+    if (split) {
+      Lb[r * K1 + Dp + c] = lo;
+      Lb[r * K1 + 2 * Dp + c] = hi;
+    }
+  }
+}
+
+// out rows n < nI: row lidx[n] of src (row length K, both operands).
+__global__ void k_rows(int nI, int K, const int32_t *__restrict__ lidx,
+                       const __nv_bfloat16 *__restrict__ src, __nv_bfloat16 *__restrict__ out) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < (int64_t)nI * K; i += nth) {
+    const int64_t n = i / K, k = i - n * K;
+    out[i] = src[(int64_t)lidx[n] * K + k];
+  }
+}
+
+int mlp_interior_operand(bs_mlp *m, int odd, cudaStream_t s) {
+  if (m->nI <= 0) return fail(BS_ERR_ARG, "mlp: input size %d is not (N+1)^3 with N >= 2", m->D);
+  if (m->int_step == m->step && m->int_odd == odd) return BS_OK;
+  if (odd)
+    if (int rc = mlp_odd_matrix(m, s)) return rc;
+  const int K = odd ? (m->split ? 3 * m->Dp : m->Dp) : (m->split ? 3 * m->H : m->H);
+  k_rows<<<stream_grid((int64_t)m->nI * K, 1, 256, 8), 256, 0, s>>>(m->nI, K, m->lidx,
+                                                                    odd ? m->Lb : m->W2b, m->Wint);
+  BS_LAUNCH_CHECK();
+  m->int_step = m->step;
+  m->int_odd = odd;
+  return BS_OK;
+}
+
+int mlp_odd_matrix(bs_mlp *m, cudaStream_t s) {
+  if (m->odd_step == m->step) return BS_OK;
+  const int64_t n = (int64_t)m->Dp * m->Dp;
+  k_odd_matrix<<<stream_grid(n, 1, 256, 8), 256, 0, s>>>(m->H, m->Dp, m->split, m->W1, m->W2,
+                                                         m->L, m->Lb);
+  BS_LAUNCH_CHECK();
+  m->odd_step = m->step;
+  return BS_OK;
+}
+
 static void free_scratch(bs_mlp *m) {
   cudaFree(m->Xb);
   cudaFree(m->Xtb);
@@ -437,6 +522,8 @@ static void free_mlp(bs_mlp *m) {
   if (!m) return;
   free_scratch(m);
   cudaFree(m->W1);
+  cudaFree(m->L);
+  cudaFree(m->lidx);
   cudaFree(m->lossp);
   free(m);
 }
@@ -468,6 +555,35 @@ int bs_mlp_create(int32_t D, int32_t H, const float *h_W1, const float *h_W2, in
   char *base = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&base, n * (8 * sizeof(float) + 7 * 2) + 256);
   if (e == cudaSuccess) e = cudaMemset(base, 0, n * (8 * sizeof(float) + 7 * 2) + 256);
+  {  // L (float Dp x Dp) then Lb (bf16 Dp x 3 Dp)
+    const size_t nl = (size_t)m->Dp * m->Dp;
+    if (e == cudaSuccess) e = cudaMalloc(&m->L, nl * (sizeof(float) + 3 * 2) + 256);
+    m->Lb = m->L ? reinterpret_cast<__nv_bfloat16 *>(m->L + nl) : nullptr;
+    m->odd_step = -1;
+  }
+  {  // interior local indices and their weight rows, when D = (N+1)^3, N >= 2
+    int Nq = 1;
+    while ((Nq + 1) * (Nq + 1) * (Nq + 1) <= D) ++Nq;
+    m->nI = (Nq * Nq * Nq == D && Nq >= 3) ? (Nq - 2) * (Nq - 2) * (Nq - 2) : 0;
+    m->int_step = -1;
+    if (m->nI > 0 && e == cudaSuccess) {
+      const int Kmax = 3 * (m->Dp > H ? m->Dp : H);
+      int32_t *hl = (int32_t *)malloc(sizeof(int32_t) * m->nI);
+      if (!hl) e = cudaErrorMemoryAllocation;
+      int q = 0;
+      for (int k = 1; hl && k < Nq - 1; ++k)
+        for (int j = 1; j < Nq - 1; ++j)
+          for (int i = 1; i < Nq - 1; ++i) hl[q++] = i + Nq * (j + Nq * k);
+      if (e == cudaSuccess)
+        e = cudaMalloc(&m->lidx, sizeof(int32_t) * m->nI + 256 + (size_t)m->nI * Kmax * 2);
+      if (e == cudaSuccess) {
+        m->Wint = reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<char *>(m->lidx) +
+                                                    ((sizeof(int32_t) * m->nI + 255) / 256) * 256);
+        e = cudaMemcpy(m->lidx, hl, sizeof(int32_t) * m->nI, cudaMemcpyHostToDevice);
+      }
+      free(hl);
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&m->lossp, sizeof(double) * kMaxPartials + 256);
   if (e == cudaSuccess) e = cudaMemset(m->lossp, 0, sizeof(double) * kMaxPartials + 256);
   if (e != cudaSuccess) {

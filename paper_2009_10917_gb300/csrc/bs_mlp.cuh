@@ -41,6 +41,20 @@ struct bs_mlp {
   float *Y, *g1, *g2;
   double *lossp;                    // per-block loss partials + counter
   unsigned int *cnt;
+  // the odd part collapsed to one matrix L = W2 W1 / 2 [Dp x Dp] (FP32, from
+  // the masters in FP64 sums) and its weight operand Lb [Dp x K1]; formed by
+  // mlp_odd_matrix, valid while odd_step == step
+  float *L;
+  __nv_bfloat16 *Lb;
+  int odd_step;
+  // element-interior outputs: when D = (N+1)^3 with N >= 2, the nI = (N-1)^3
+  // local indices lidx of the interior nodes and Wint [nI x max(K1, K2)], the
+  // weight rows that produce them (rows of Lb for the odd part, of W2b for
+  // the full network), formed by mlp_interior_operand
+  int nI;
+  int32_t *lidx;
+  __nv_bfloat16 *Wint;
+  int int_step, int_odd;
 };
 
 namespace bs {
@@ -50,7 +64,9 @@ enum GemmEpi {
   EPI_HIDDEN = 1,    // a = relu ? max(acc, 0) : acc; out_b16[m ldc + n] = bf16(a), and
                      // with split > 0 also hi at +split and lo = bf16(a - hi) at +2 split
   EPI_MASK_BF16 = 2, // out_b16[m ldc + n] = mask[m ldmask + n] > 0 ? bf16(acc) : 0
-  EPI_SCALE_F64 = 3  // n < nvalid: out_f64[m ldc + n] = acc * scale[m]
+  EPI_SCALE_F64 = 3, // n < nvalid: out_f64[m ldc + n] = acc * scale[m]
+  EPI_SCATTER_F64 = 4 // n < nvalid, gid = ids[order[m] np + lidx[n]] >= 0:
+                      // out_f64[gid] = acc * scale[m]
 };
 
 struct GemmArgs {
@@ -63,6 +79,8 @@ struct GemmArgs {
   const __nv_bfloat16 *mask;
   int ldmask, relu, split;
   const float *scale;
+  const int32_t *ids, *order, *lidx;  // EPI_SCATTER_F64: map, row -> element, local indices
+  int np;
   const CgState *st;  // optional: skip the launch when a solve has stopped
 };
 
@@ -80,5 +98,9 @@ __device__ __forceinline__ void bf16_split(float v, __nv_bfloat16 &hi, __nv_bflo
 }
 // Training/inference scratch for batches (or element counts) up to B rows.
 int mlp_ensure(bs_mlp *m, int64_t B);
+// L = W2 W1 / 2 and its operand Lb, if the weights changed since last formed.
+int mlp_odd_matrix(bs_mlp *m, cudaStream_t s);
+// Wint for the odd part (odd) or the full network's output layer, if stale.
+int mlp_interior_operand(bs_mlp *m, int odd, cudaStream_t s);
 
 }  // namespace bs

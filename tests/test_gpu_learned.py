@@ -154,31 +154,41 @@ def test_fpcg_zero_network_equals_no_network():
 
 
 def test_fpcg_with_a_linear_correction_matches_oracle():
-    """A damped element Jacobi sweep M u as the network's odd part (W1 = I,
-    W2 = 2 M): the GPU's flexible PCG (BF16x3) follows the oracle's and meets
-    the tolerance on the FP64 true residual."""
-    m, Z, P = _problem(3, 2, 1.0)
-    S, M = fem_ref.element_matrices(2, m.h)
-    Ae = S + M
+    """The exact element-interior map u_I -> A_II^-1 D_I u_I - u_I as the
+    network's odd part (W1 = I, W2 = 2 M): the GPU's flexible PCG (BF16x3)
+    follows the oracle's, meets the tolerance on the FP64 true residual and
+    needs fewer iterations than Jacobi-PCG."""
+    N, lam = 5, 1e-2
+    coef = synth.lognormal(4 ** 3, 2)
+    m, Z, P = _problem(4, N, lam, coef)
+    S, M = fem_ref.element_matrices(N, m.h)  # c = 1: the map hardly depends on c
+    Ae = S + lam * M
     Np = m.Np
-    Mlin = 0.5 * (np.eye(Np) - Ae / np.diag(Ae)[:, None])
-    H = 32
+    I = np.array([i + 6 * (j + 6 * k) for k in range(1, 5) for j in range(1, 5)
+                  for i in range(1, 5)])
+    Mint = np.zeros((Np, Np))
+    Mint[np.ix_(I, I)] = np.linalg.solve(Ae[np.ix_(I, I)], np.diag(np.diag(Ae)[I])) - np.eye(64)
+    H = 224
     W1 = np.zeros((H, Np), np.float32)
     W1[:Np] = np.eye(Np)
     W2 = np.zeros((Np, H), np.float32)
-    W2[:, :Np] = 2 * Mlin
+    W2[:, :Np] = 2 * Mint
     net = bs.MLP(W1, W2, split=True)
-    bh = synth.uniform(m.NG, 6)
+    bh = synth.uniform(m.NG, 5)
     b = torch.from_numpy(bh).cuda()
-    x, info = bs.fpcg_learned(P, net, b, tol=1e-10, flags=bs.BS_FPCG_ODD)
+    x, info = bs.fpcg_learned(P, net, b, tol=1e-8, flags=bs.BS_FPCG_ODD)
     assert info["rc"] == 0 and info["outer"] == 0
-    r = bh - oracle.apply_A(m.E, 2, m.h, 1.0, m.ids, m.NG, x.cpu().numpy())
-    assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(bh)
-    _, ito, _, _ = oracle.fpcg(m.E, 2, m.h, 1.0, m.ids, m.NG, bh, W1, W2,
-                               prec=oracle.PREC_BF16X3, odd=True, tol=1e-10)
+    r = bh - oracle.apply_A(m.E, N, m.h, lam, m.ids, m.NG, x.cpu().numpy(), coef=coef)
+    assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(bh)
+    _, ito, _, _ = oracle.fpcg(m.E, N, m.h, lam, m.ids, m.NG, bh, W1, W2,
+                               prec=oracle.PREC_BF16X3, odd=True, tol=1e-8, coef=coef)
     assert abs(info["iterations"] - ito) <= max(3, 0.1 * ito)
-    _, ij = P.cg(b, tol=1e-10, flags=bs.BS_CG_JACOBI)
-    assert info["iterations"] < ij["iterations"]
+    _, ij = P.cg(b, tol=1e-8, flags=bs.BS_CG_JACOBI)
+    assert info["iterations"] < 0.8 * ij["iterations"]  # 254 vs 371 in the oracle
+    # the full network of this W1, W2 is the same map plus an even part: it
+    # runs through the two-layer path and still converges
+    _, inf2 = bs.fpcg_learned(P, net, b, tol=1e-8, maxit=20000, check=False)
+    assert inf2["rc"] == 0
 
 
 @pytest.mark.parametrize("N", [2, 3, 5])

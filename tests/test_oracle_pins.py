@@ -448,22 +448,56 @@ def test_fpcg_with_zero_correction_is_jacobi_pcg():
     np.testing.assert_allclose(rr[:k], rrj[:k], rtol=1e-8)
 
 
-def test_fpcg_with_exact_local_inverse_beats_jacobi():
-    """A correction that reproduces an element-block solve is a stronger
-    preconditioner than Jacobi: FPCG must then need fewer iterations."""
-    m = synth.Mesh(2, 2, seed=1)
-    A_e = fem_ref.element_matrices(2, m.h)
-    Ae = A_e[0] + 1e-2 * A_e[1]
-    # linear map u -> Ae^-1 (diag(Ae) u) - u, realised exactly with ReLU pairs
+def test_fpcg_interior_inverse_is_block_jacobi_pcg():
+    """With the exact element-interior map u_I -> A_II^-1 D_I u_I - u_I as the
+    network's odd part, the learned preconditioner is block Jacobi: the
+    interior block of each element inverted, D^-1 elsewhere.  FPCG must take
+    the steps of a dense numpy PCG with that matrix (independent assembly),
+    and fewer than Jacobi-PCG."""
+    N, lam = 5, 1e-2
+    m = synth.Mesh(2, N, seed=1)
+    A = fem_ref.assemble(m, lam)
+    S, M = fem_ref.element_matrices(N, m.h)
+    Ae = S + lam * M
+    I = _interior_index(N)
     Np = m.Np
-    Mlin = np.linalg.solve(Ae, np.diag(np.diag(Ae))) - np.eye(Np)
-    W1 = np.concatenate([np.eye(Np), -np.eye(Np)]).astype(np.float32)
-    W2 = np.concatenate([Mlin, -Mlin], axis=1).astype(np.float32)
+    d = np.diag(Ae)
+    Mint = np.zeros((Np, Np))
+    Mint[np.ix_(I, I)] = np.linalg.solve(Ae[np.ix_(I, I)], np.diag(d[I])) - np.eye(len(I))
+    W1 = np.eye(Np, dtype=np.float32)
+    W2 = (2 * Mint).astype(np.float32)
     b = synth.uniform(m.NG, 3)
-    _, it, _, fb = oracle.fpcg(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, W1, W2, prec=oracle.PREC_FP64,
-                               tol=1e-10, maxit=2000)
-    _, itj, _ = oracle.pcg_jacobi(m.E, 2, m.h, 1e-2, m.ids, m.NG, b, tol=1e-10, maxit=2000)
-    assert it < itj and fb == 0
+    _, it, rr, fb = oracle.fpcg(m.E, N, m.h, lam, m.ids, m.NG, b, W1, W2,
+                                prec=oracle.PREC_FP64, odd=True, tol=1e-10, maxit=2000)
+    # dense block-Jacobi PCG
+    Minv = np.diag(1.0 / np.diag(A))
+    for e in range(m.E):
+        g = m.ids[e * Np:(e + 1) * Np][I]
+        Minv[np.ix_(g, g)] = np.linalg.inv(A[np.ix_(g, g)])
+    x = np.zeros(m.NG)
+    r = b.copy()
+    z = Minv @ r
+    p = z.copy()
+    rz = r @ z
+    hist = [r @ r]
+    k = 0
+    while hist[-1] > 1e-20 * (b @ b) and k < 2000:
+        Ap = A @ p
+        a = rz / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        hist.append(r @ r)
+        k += 1
+        z = Minv @ r
+        rzn = r @ z
+        p = z + rzn / rz * p
+        rz = rzn
+    # the network takes float inputs and float weights (relative 2^-24), so
+    # the two agree to about 1e-7 per step and drift slowly
+    np.testing.assert_allclose(rr[:8], hist[:8], rtol=1e-6)
+    assert fb == 0 and abs(it - k) <= max(2, 0.1 * k)
+    _, itj, _ = oracle.pcg_jacobi(m.E, N, m.h, lam, m.ids, m.NG, b, tol=1e-10, maxit=2000)
+    assert it < itj
 
 
 def _interior_index(N):
