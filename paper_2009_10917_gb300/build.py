@@ -45,12 +45,19 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__])
 
 
-def source_digest() -> str:
-    """SHA-256 over the kernel sources and headers (identifies a build)."""
+# Sources of the seven BS kernels (BS1-BS7) and the device helpers they
+# include (the C header holds declarations only).
+STREAM_SOURCES = ("bs_internal.cuh", "bs_stream.cuh", "bs_stream.cu", "bs_gs.cuh",
+                  "bs_gather.cuh", "bs_gs.cu")
+
+
+def source_digest(names=None) -> str:
+    """SHA-256 over the kernel sources and headers (identifies a build), or
+    over the named files only (e.g. STREAM_SOURCES)."""
     import hashlib
     h = hashlib.sha256()
     for d in sorted(_deps()):
-        if d == __file__:
+        if d == __file__ or (names is not None and os.path.basename(d) not in names):
             continue
         with open(d, "rb") as f:
             h.update(os.path.basename(d).encode() + b"\0" + f.read())
