@@ -167,6 +167,16 @@ int bs_apply_local(const bs_problem *prob, const double *uL, double *AuL,
 /* diag(A) = Z^T diag(A_L) into d_diag[NG]. */
 int bs_diag_A(const bs_problem *prob, double *d_diag, void *stream);
 
+/* bs_apply_A with the element operator in float-float arithmetic (no
+ * counterpart in the paper): GB300 executes FP64 at about 1/64 of its FP32
+ * rate, so each input is split exactly into a pair of floats by integer
+ * operations, the contractions accumulate error-free products of the high
+ * parts with TwoSum on the FP32 pipes, and only the final combination of a
+ * node is FP64.  Error per node: a few units of 2^-46 times sum |K| |u|
+ * (about 64 times the FP64 operator's); inputs below 2^-102 in magnitude
+ * count as zero.  The gather is the same as bs_apply_A's. */
+int bs_apply_A_ff(const bs_problem *prob, const double *p, double *Ap, void *stream);
+
 /* ------------------------------------------------------------ CG */
 
 enum {
@@ -174,7 +184,8 @@ enum {
   BS_CG_JACOBI = 2,      /* Jacobi preconditioner z = diag(A)^-1 r         */
   BS_CG_GRAPH = 4,       /* replay the iteration as a captured CUDA graph  */
   BS_CG_X0 = 8,          /* x holds the initial guess (else x0 = 0)        */
-  BS_CG_REFINED_F32 = 32 /* batched: FP32 inner CG, FP64 refinement        */
+  BS_CG_REFINED_F32 = 32, /* batched: FP32 inner CG, FP64 refinement       */
+  BS_CG_FF_OPERATOR = 256 /* the float-float operator of bs_apply_A_ff      */
 };
 
 typedef struct {
@@ -192,8 +203,11 @@ typedef struct {
  * after maxit iterations; the convergence flag is computed on the device and
  * read back every few iterations.  d_hist (DEVICE, may be NULL) receives
  * 3*(maxit+1) doubles: alpha_j at [3j], beta_j at [3j+1], r_{j+1}.r_{j+1} at
- * [3j+2].  Synchronises `stream` before returning; info (host) may be NULL.
- * Returns BS_ERR_NOT_CONVERGED if maxit is reached without BS_CG_FIXED_ITERS,
+ * [3j+2].  flags: BS_CG_FIXED_ITERS, BS_CG_JACOBI, BS_CG_GRAPH, BS_CG_X0,
+ * BS_CG_FF_OPERATOR (every A p with the float-float element operator of
+ * bs_apply_A_ff; vectors, reductions and updates stay FP64).  Synchronises
+ * `stream` before returning; info (host) may be NULL.  Returns
+ * BS_ERR_NOT_CONVERGED if maxit is reached without BS_CG_FIXED_ITERS,
  * BS_ERR_BREAKDOWN on p.Ap <= 0. */
 int bs_cg_solve(const bs_problem *prob, const double *b, double *x, double tol,
                 int32_t maxit, int32_t flags, double *d_hist,
@@ -327,7 +341,7 @@ int bs_mlp_pairs(const bs_problem *prob, const double *d_r, int64_t count,
  * without halving it on these operators) the solve restarts from the current x
  * with Jacobi for good (info->outer = the iteration of that switch, 0 if
  * none).  Stop: r.r <= tol^2 b.b or maxit.  flags: BS_CG_GRAPH,
- * BS_FPCG_ODD, BS_FPCG_NO_JUDGE.  The network's input size must be (N+1)^3,
+ * BS_FPCG_ODD, BS_FPCG_NO_JUDGE, BS_CG_FF_OPERATOR.  The network's input size must be (N+1)^3,
  * 2 <= N <= 9.  Synchronises `stream`.  Returns BS_ERR_NOT_CONVERGED or
  * BS_ERR_BREAKDOWN as bs_cg_solve does. */
 int bs_fpcg_learned(const bs_problem *prob, bs_mlp *mlp, const double *b, double *x,

@@ -33,6 +33,7 @@ BS_CG_JACOBI = 2
 BS_CG_GRAPH = 4
 BS_CG_X0 = 8
 BS_CG_REFINED_F32 = 32
+BS_CG_FF_OPERATOR = 256
 BS_MLP_BF16X3 = 1
 BS_MLP_ODD = 2
 BS_FPCG_ODD = 64
@@ -91,6 +92,7 @@ _SIGS = {
     "bs_problem_create": (ctypes.c_int, [_vp, _d, _d, _vp, _pp]),
     "bs_problem_destroy": (ctypes.c_int, [_vp]),
     "bs_apply_A": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_apply_A_ff": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bs_apply_local": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bs_diag_A": (ctypes.c_int, [_vp, _vp, _vp]),
     "bs_cg_solve": (ctypes.c_int, [_vp, _vp, _vp, _d, _i32, _i32, _vp,
@@ -304,6 +306,12 @@ class Problem:
     def apply_A(self, p, Ap=None):
         Ap = torch.empty_like(p) if Ap is None else Ap
         _check(lib().bs_apply_A(self.handle, _ptr(p), _ptr(Ap), _stream()), "bs_apply_A")
+        return Ap
+
+    def apply_A_ff(self, p, Ap=None):
+        """A p with the float-float element operator (bs_apply_A_ff)."""
+        Ap = torch.empty_like(p) if Ap is None else Ap
+        _check(lib().bs_apply_A_ff(self.handle, _ptr(p), _ptr(Ap), _stream()), "bs_apply_A_ff")
         return Ap
 
     def apply_local(self, uL, AuL=None):

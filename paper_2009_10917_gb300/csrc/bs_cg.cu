@@ -14,7 +14,7 @@
 #include <chrono>
 #include <cmath>
 
-#include "bs_op.cuh"
+#include "bs_op_ff.cuh"
 
 namespace bs {
 
@@ -161,14 +161,16 @@ static int pcg_update_launch(const bs_problem *P, double *x, int init, cudaStrea
   return BS_OK;
 }
 
-// One CG iteration (four launches).
-static int cg_iteration(const bs_problem *P, double *x, bool precond, cudaStream_t s) {
+// One CG iteration (four launches).  ff: the float-float element operator.
+static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, cudaStream_t s) {
   const bs_map *m = P->map;
   CgVecs v = vecs(P);
   CgState *st = P->d_state;
   const double g = 0.5 * P->h, mlam = P->lambda * g * g * g;
-  int rc = launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, P->d_ApL,
-                                         P->d_tab, P->d_coef, g, mlam, st, s);
+  int rc = ff ? launch_ax_local_ff<true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, P->d_ApL,
+                                         P->d_tabff, P->d_coef, g, mlam, st, s)
+              : launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p,
+                                              P->d_ApL, P->d_tab, P->d_coef, g, mlam, st, s);
   if (rc) return rc;
   rc = launch_gather<double, true, EpAlpha>(m, P->d_ApL, v.Ap, v.p, P->d_partials, P->d_counter,
                                             EpAlpha{st, precond ? 1 : 0}, st, s);
@@ -184,8 +186,9 @@ static int cg_iteration(const bs_problem *P, double *x, bool precond, cudaStream
                              Scalar<double>{0.0, &st->beta}, v.p, st, s);
 }
 
-static int capture_chunk(bs_problem *P, double *x, bool precond, int chunk) {
-  const void *key[4] = {x, (const void *)(intptr_t)precond, (const void *)(intptr_t)chunk,
+static int capture_chunk(bs_problem *P, double *x, bool precond, bool ff, int chunk) {
+  const void *key[4] = {x, (const void *)(intptr_t)((precond ? 1 : 0) | (ff ? 2 : 0)),
+                        (const void *)(intptr_t)chunk,
                         (const void *)P->map};
   if (P->graph && key[0] == P->graph_key[0] && key[1] == P->graph_key[1] &&
       key[2] == P->graph_key[2] && key[3] == P->graph_key[3])
@@ -197,7 +200,7 @@ static int capture_chunk(bs_problem *P, double *x, bool precond, int chunk) {
   cudaStream_t cs = P->cap_stream;
   BS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   int rc = BS_OK;
-  for (int c = 0; c < chunk && rc == BS_OK; ++c) rc = cg_iteration(P, x, precond, cs);
+  for (int c = 0; c < chunk && rc == BS_OK; ++c) rc = cg_iteration(P, x, precond, ff, cs);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   if (rc != BS_OK) {
@@ -237,6 +240,7 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
   cudaStream_t s = as_stream(stream);
   const bool fixed = flags & BS_CG_FIXED_ITERS;
   const bool precond = flags & BS_CG_JACOBI;
+  const bool ff = flags & BS_CG_FF_OPERATOR;
   CgVecs v = vecs(P);
   CgState *st = P->d_state;
   int rc = BS_OK;
@@ -253,7 +257,7 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
     // r_0 = b - A x_0
     BS_TRY(launch_copy<double>(NG, b, v.r, s));
     if (flags & BS_CG_X0) {
-      BS_TRY(bs_apply_A(P, x, v.Ap, stream));
+      BS_TRY(ff ? bs_apply_A_ff(P, x, v.Ap, stream) : bs_apply_A(P, x, v.Ap, stream));
       BS_TRY(launch_axpy<double>(NG, Scalar<double>{-1.0, nullptr}, v.Ap,
                                  Scalar<double>{1.0, nullptr}, v.r, nullptr, s));
     }
@@ -273,12 +277,12 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
     const bool graph = flags & BS_CG_GRAPH;
     const int chunk = maxit < 8 ? (maxit < 1 ? 1 : maxit) : 8;
     int launched = 0;
-    if (graph && maxit > 0) BS_TRY(capture_chunk(P, x, precond, chunk));
+    if (graph && maxit > 0) BS_TRY(capture_chunk(P, x, precond, ff, chunk));
     while (launched < maxit) {
       if (graph) {
         BS_CUDA_TRY(cudaGraphLaunch(P->graph, s));
       } else {
-        for (int c = 0; c < chunk; ++c) BS_TRY(cg_iteration(P, x, precond, s));
+        for (int c = 0; c < chunk; ++c) BS_TRY(cg_iteration(P, x, precond, ff, s));
       }
       launched += chunk;
       BS_CUDA_TRY(cudaMemcpyAsync(P->h_state, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));

@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "bs_mlp.cuh"
+#include "bs_op_ff.cuh"
 
 namespace bs {
 
@@ -318,13 +319,16 @@ static int precondition(const bs_problem *P, bs_mlp *mlp, int odd, int init, cud
   return BS_OK;
 }
 
-static int fpcg_iteration(const bs_problem *P, bs_mlp *mlp, int odd, double *x, cudaStream_t s) {
+static int fpcg_iteration(const bs_problem *P, bs_mlp *mlp, int odd, bool ff, double *x,
+                          cudaStream_t s) {
   const bs_map *m = P->map;
   FpVecs v = fpvecs(P);
   CgState *st = P->d_state;
   const double g = 0.5 * P->h, mlam = P->lambda * g * g * g;
-  int rc = launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, P->d_ApL,
-                                         P->d_tab, P->d_coef, g, mlam, st, s);
+  int rc = ff ? launch_ax_local_ff<true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, P->d_ApL,
+                                         P->d_tabff, P->d_coef, g, mlam, st, s)
+              : launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p,
+                                              P->d_ApL, P->d_tab, P->d_coef, g, mlam, st, s);
   if (!rc)
     rc = launch_gather<double, true, EpAlphaRz>(m, P->d_ApL, v.Ap, v.p, P->d_partials,
                                                 P->d_counter, EpAlphaRz{st}, st, s);
@@ -545,8 +549,9 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
   BS_CUDA_TRY(cudaGetDevice(&dev));
   BS_ARG(dev == P->device, "bs_fpcg_learned: problem on another device");
   BS_ARG(maxit >= 0 && tol >= 0.0 && std::isfinite(tol), "bs_fpcg_learned: bad tol or maxit");
-  BS_ARG((flags & ~(BS_CG_GRAPH | BS_FPCG_ODD | BS_FPCG_NO_JUDGE)) == 0,
+  BS_ARG((flags & ~(BS_CG_GRAPH | BS_FPCG_ODD | BS_FPCG_NO_JUDGE | BS_CG_FF_OPERATOR)) == 0,
          "bs_fpcg_learned: unknown flags 0x%x", (unsigned)flags);
+  const bool ff = flags & BS_CG_FF_OPERATOR;
   const bool judge = !(flags & BS_FPCG_NO_JUDGE);
   const int odd = (flags & BS_FPCG_ODD) ? 1 : 0;
   const bs_map *m = P->map;
@@ -588,7 +593,7 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
     cudaStream_t cs = P->cap_stream;
     BS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int r2 = BS_OK;
-    for (int c = 0; c < chunk && !r2; ++c) r2 = fpcg_iteration(P, net, odd, x, cs);
+    for (int c = 0; c < chunk && !r2; ++c) r2 = fpcg_iteration(P, net, odd, ff, x, cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (!r2 && e != cudaSuccess) r2 = fail(BS_ERR_CUDA, "fpcg capture: %s", cudaGetErrorString(e));
@@ -615,7 +620,7 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
     if (graph) {
       if (cudaGraphLaunch(gexec, s) != cudaSuccess) rc = fail(BS_ERR_CUDA, "fpcg graph launch");
     } else {
-      for (int c = 0; c < chunk && !rc; ++c) rc = fpcg_iteration(P, net, odd, x, s);
+      for (int c = 0; c < chunk && !rc; ++c) rc = fpcg_iteration(P, net, odd, ff, x, s);
     }
     if (rc) break;
     if (cudaMemcpyAsync(P->h_state, st, sizeof(CgState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -6,7 +6,7 @@
 #include <cstring>
 #include <vector>
 
-#include "bs_op.cuh"
+#include "bs_op_ff.cuh"
 
 namespace bs {
 
@@ -121,6 +121,7 @@ static void free_problem(bs_problem *p) {
   cudaFree(p->d_coef);
   cudaFree(p->d_tab);
   cudaFree(p->d_tabf);
+  cudaFree(p->d_tabff);
   cudaFree(p->d_ApL);
   cudaFree(p->d_vec);
   cudaFree(p->d_state);
@@ -160,12 +161,21 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
   stiffness_1d(N, w, D, K);
   OpTab<double> tab{};
   OpTab<float> tabf{};
+  OpTabFF tabff{};
+  // float pairs v = hi + lo (hi = v rounded to float, lo = the rest rounded)
+  auto split = [](double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
   for (int i = 0; i < Nq; ++i) {
     tab.w[i] = w[i];
     tabf.w[i] = (float)w[i];
+    tabff.w[i] = w[i];
     for (int m = 0; m < Nq; ++m) {
       tab.K[i * Nq + m] = K[i * Nq + m];
       tabf.K[i * Nq + m] = (float)K[i * Nq + m];
+      split(K[i * Nq + m], tabff.Kh[i * Nq + m], tabff.Kl[i * Nq + m]);
+      split(w[i] * w[m], tabff.Wh[i * Nq + m], tabff.Wl[i * Nq + m]);
     }
   }
   const int64_t NL = map->NL, NG = map->NG;
@@ -177,6 +187,8 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
   if (e == cudaSuccess) e = cudaMalloc(&p->d_tabf, sizeof(tabf));
   if (e == cudaSuccess) e = cudaMemcpy(p->d_tab, &tab, sizeof(tab), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_tabf, &tabf, sizeof(tabf), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_tabff, sizeof(tabff));
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_tabff, &tabff, sizeof(tabff), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_ApL, sizeof(double) * (NL + 2));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_vec, sizeof(double) * 6 * (NG + 2));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_state, sizeof(CgState));
@@ -217,6 +229,19 @@ int bs_apply_A(const bs_problem *p, const double *x, double *Ax, void *stream) {
   if (int rc = launch_ax_local<double, true>(p->N, p->map->E, p->map->d_elem_order,
                                              p->map->d_ids, x, p->d_ApL, p->d_tab, p->d_coef, g,
                                              mlam, nullptr, s))
+    return rc;
+  return launch_gather<double, false, EpNone>(p->map, p->d_ApL, Ax, nullptr, nullptr, nullptr,
+                                              EpNone{}, nullptr, s);
+}
+
+int bs_apply_A_ff(const bs_problem *p, const double *x, double *Ax, void *stream) {
+  if (int rc = check_prob(p, "bs_apply_A_ff")) return rc;
+  if (p->map->NG == 0) return BS_OK;
+  BS_ARG(x && Ax, "bs_apply_A_ff: NULL vector");
+  const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
+  cudaStream_t s = as_stream(stream);
+  if (int rc = launch_ax_local_ff<true>(p->N, p->map->E, p->map->d_elem_order, p->map->d_ids, x,
+                                        p->d_ApL, p->d_tabff, p->d_coef, g, mlam, nullptr, s))
     return rc;
   return launch_gather<double, false, EpNone>(p->map, p->d_ApL, Ax, nullptr, nullptr, nullptr,
                                               EpNone{}, nullptr, s);

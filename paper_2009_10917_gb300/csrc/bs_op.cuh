@@ -155,6 +155,8 @@ int launch_ax_local(int N, int64_t E, const int32_t *order, const int32_t *ids, 
   return BS_OK;
 }
 
+struct OpTabFF;  // bs_op_ff.cuh
+
 }  // namespace bs
 
 // A problem: the map, the geometry and the device scratch of the solvers.
@@ -166,6 +168,7 @@ struct bs_problem {
   double *d_coef;                 // [E] or NULL
   bs::OpTab<double> *d_tab;       // FP64 tables
   bs::OpTab<float> *d_tabf;       // FP32 tables
+  bs::OpTabFF *d_tabff;           // float-pair tables of the float-float operator
   double *d_ApL;                  // [NL] local operator output (FP64 or FP32 view)
   double *d_vec;                  // 6 x [NG]: r, p, Ap, z, dinv, spare
   bs::CgState *d_state;

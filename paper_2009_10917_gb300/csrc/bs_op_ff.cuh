@@ -1,0 +1,215 @@
+// bs_op_ff.cuh -- the element operator of bs_op.cuh evaluated in float-float
+// arithmetic on the FP32 pipes.
+//
+// GB300 runs FP64 at about 1/64 of its FP32 rate (measured: 627 G DFMA/s
+// against 39 T FFMA/s), so the FP64 operator -- 3(N+1) + ~8 FP64 operations
+// per local node -- is FP64-pipe bound, far from the HBM roofline.  Here every
+// input double u is split exactly, by integer operations (no conversion
+// instructions, which share the FP64 pipe), into uh = u truncated to 24
+// significant bits and ul = the remaining bits rounded to a float
+// (|u - uh - ul| <= 2^-48 |u|); the 1-D stiffness K and the weight products
+// w_a w_b are split the same way on the host.  Each contraction
+// sum_m K_im u_m is then accumulated as an unevaluated float pair: the product
+// of the high parts exactly (FMUL and the FFMA of its rounding error), the
+// cross terms Kh ul + Kl uh in a float, and the sum of the high products by
+// TwoSum (Knuth).  The error of a node's result is a few units of 2^-46 times
+// sum |K| |u| (about 64 times FP64's), far below the tolerances CG is run to.
+// Per node the FP64 pipe does four operations: joining the float pair, the
+// mass term and the final fused multiply-add.
+//
+// Inputs with |u| < 2^-102 are taken as zero (so are the low parts below
+// float's normal range); |u| >= 2^127 becomes infinite, which CG reports as a
+// breakdown.
+#pragma once
+
+#include "bs_op.cuh"
+
+namespace bs {
+
+// (FF, the float pair hi + lo, is defined with the FP32 reductions.)
+
+// Split tables: K = Kh + Kl and W[a*Nq + b] = w_a w_b = Wh + Wl (float
+// pairs of the double values), and the weights in double for the mass term.
+struct OpTabFF {
+  float Kh[kMaxNq * kMaxNq], Kl[kMaxNq * kMaxNq];
+  float Wh[kMaxNq * kMaxNq], Wl[kMaxNq * kMaxNq];
+  double w[kMaxNq];
+};
+
+// x = h + l exactly up to 2^-48 |x| (see the header comment); integer and
+// FP32 operations only.
+__device__ __forceinline__ FF ff_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned E = (hw >> 20) & 0x7ffu;
+  const unsigned sign = hw & 0x80000000u;
+  if (E < 921u) return FF{0.f, 0.f};                                  // |x| < 2^-102
+  if (E > 1150u) return FF{__uint_as_float(sign | 0x7f800000u), 0.f};  // |x| >= 2^127
+  const float h =
+      __uint_as_float(sign | ((E - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  // the low 29 bits, rounded to 23, times 2^(E - 1069): base = 2^(E - 1046)
+  // as a float; the bit pattern base + rr is base (1 + rr 2^-23), so the
+  // difference is rr 2^(E - 1069) exactly (rr = 2^23 carries into the
+  // exponent and still gives that value)
+  const unsigned rr = ((lw & 0x1fffffffu) + 32u) >> 6;
+  const unsigned base = (E - 919u) << 23;
+  const float l = __uint_as_float(
+      __float_as_uint(__uint_as_float(base + rr) - __uint_as_float(base)) | sign);
+  return FF{h, l};
+}
+
+// A normal or zero float as a double by assembling its bits (no conversion
+// instruction); subnormals (below 2^-126) flush to zero.
+__device__ __forceinline__ double ff_widen(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  if (e == 0xffu) return (double)v;  // inf / nan: rare, let the conversion handle it
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// s += (a + al)(b + bl), dropping al bl: the high product exactly (p + e),
+// the rest in a float, the high parts summed by TwoSum.
+__device__ __forceinline__ void ff_fma(FF &s, float a, float al, float b, float bl) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float c = fmaf(a, bl, fmaf(al, b, e));
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo = s.lo + (err + c);
+}
+
+// out = A_L in on elements slot0 .. slot0 + EPB - 1, as ax_elements.
+template <int NQ, bool GATHER_IN>
+__device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
+                                               const int32_t *__restrict__ order,
+                                               const int32_t *__restrict__ ids,
+                                               const double *__restrict__ in,
+                                               double *__restrict__ out,
+                                               const OpTabFF *__restrict__ tab,
+                                               const double *__restrict__ coef, double g,
+                                               double mlam, float *s_uh_all, float *s_ul_all,
+                                               float *s_K, double *s_w) {
+  using S = OpShape<NQ>;
+  constexpr int NQ2 = NQ * NQ;
+  float *s_Kh = s_K, *s_Kl = s_K + NQ2, *s_Wh = s_K + 2 * NQ2, *s_Wl = s_K + 3 * NQ2;
+  __syncthreads();
+  for (int t = threadIdx.x; t < NQ2; t += blockDim.x) {
+    const int a = t / NQ, b = t % NQ;
+    s_Kh[t] = tab->Kh[a * NQ + b];
+    s_Kl[t] = tab->Kl[a * NQ + b];
+    s_Wh[t] = tab->Wh[a * NQ + b];
+    s_Wl[t] = tab->Wl[a * NQ + b];
+  }
+  for (int t = threadIdx.x; t < NQ; t += blockDim.x) s_w[t] = tab->w[t];
+  const int le = threadIdx.x / NQ2;
+  const int ij = threadIdx.x - le * NQ2;
+  const int i = ij % NQ, j = ij / NQ;
+  const int64_t slot = slot0 + le;
+  const bool active = le < S::EPB && slot < E;
+  const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  float *uh = s_uh_all + (le < S::EPB ? le : 0) * S::NP;
+  float *ul = s_ul_all + (le < S::EPB ? le : 0) * S::NP;
+  float rh[NQ], rl[NQ];
+  double ud[NQ];
+  if (active) {
+    const int64_t base = e * S::NP + ij;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      double v;
+      if (GATHER_IN) {
+        const int32_t id = __ldcs(ids + base + k * NQ2);
+        v = id >= 0 ? in[id] : 0.0;
+      } else {
+        v = __ldcs(in + base + k * NQ2);
+      }
+      ud[k] = v;
+      const FF f = ff_split(v);
+      rh[k] = f.hi;
+      rl[k] = f.lo;
+      uh[ij + k * NQ2] = f.hi;
+      ul[ij + k * NQ2] = f.lo;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const double cg = (coef ? coef[e] : 1.0) * g;
+  const double mwij = mlam * (s_w[i] * s_w[j]);
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    FF ar{0.f, 0.f}, as{0.f, 0.f}, at{0.f, 0.f};
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int lr = m + NQ * j + NQ2 * k, ls = i + NQ * m + NQ2 * k;
+      ff_fma(ar, s_Kh[i * NQ + m], s_Kl[i * NQ + m], uh[lr], ul[lr]);
+      ff_fma(as, s_Kh[j * NQ + m], s_Kl[j * NQ + m], uh[ls], ul[ls]);
+      ff_fma(at, s_Kh[k * NQ + m], s_Kl[k * NQ + m], rh[m], rl[m]);
+    }
+    // (w_j w_k) ar + (w_i w_k) as + (w_i w_j) at
+    FF t{0.f, 0.f};
+    ff_fma(t, s_Wh[j * NQ + k], s_Wl[j * NQ + k], ar.hi, ar.lo);
+    ff_fma(t, s_Wh[i * NQ + k], s_Wl[i * NQ + k], as.hi, as.lo);
+    ff_fma(t, s_Wh[i * NQ + j], s_Wl[i * NQ + j], at.hi, at.lo);
+    const double stiff = ff_widen(t.hi) + ff_widen(t.lo);
+    const double mass = (mwij * s_w[k]) * ud[k];
+    __stcs(out + e * S::NP + ij + k * NQ2, fma(cg, stiff, mass));
+  }
+}
+
+template <int NQ, bool GATHER_IN>
+__global__ void __launch_bounds__(OpShape<NQ>::THREADS)
+    k_ax_local_ff(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
+                  const double *__restrict__ in, double *__restrict__ out,
+                  const OpTabFF *__restrict__ tab, const double *__restrict__ coef, double g,
+                  double mlam, const CgState *st) {
+  using S = OpShape<NQ>;
+  __shared__ float s_uh[S::EPB * S::NP];
+  __shared__ float s_ul[S::EPB * S::NP];
+  __shared__ float s_K[4 * NQ * NQ];
+  __shared__ double s_w[NQ];
+  if (cg_halted(st)) return;
+  ax_elements_ff<NQ, GATHER_IN>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out, tab, coef,
+                                g, mlam, s_uh, s_ul, s_K, s_w);
+}
+
+template <bool GATHER_IN>
+int launch_ax_local_ff(int N, int64_t E, const int32_t *order, const int32_t *ids,
+                       const double *in, double *out, const OpTabFF *tab, const double *coef,
+                       double g, double mlam, const CgState *st, cudaStream_t s) {
+  if (E == 0) return BS_OK;
+#define BS_AXFF_CASE(NQ)                                                              \
+  case NQ: {                                                                          \
+    using Sh = OpShape<NQ>;                                                           \
+    const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                 \
+    k_ax_local_ff<NQ, GATHER_IN><<<(unsigned)grid, Sh::THREADS, 0, s>>>(              \
+        E, order, ids, in, out, tab, coef, g, mlam, st);                              \
+    break;                                                                            \
+  }
+  switch (N + 1) {
+    BS_AXFF_CASE(2)
+    BS_AXFF_CASE(3)
+    BS_AXFF_CASE(4)
+    BS_AXFF_CASE(5)
+    BS_AXFF_CASE(6)
+    BS_AXFF_CASE(7)
+    BS_AXFF_CASE(8)
+    BS_AXFF_CASE(9)
+    BS_AXFF_CASE(10)
+    BS_AXFF_CASE(11)
+    BS_AXFF_CASE(12)
+    BS_AXFF_CASE(13)
+    BS_AXFF_CASE(14)
+    BS_AXFF_CASE(15)
+    BS_AXFF_CASE(16)
+    default:
+      return fail(BS_ERR_ARG, "degree %d unsupported", N);
+  }
+#undef BS_AXFF_CASE
+  BS_LAUNCH_CHECK();
+  return BS_OK;
+}
+
+}  // namespace bs

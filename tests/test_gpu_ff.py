@@ -1,0 +1,80 @@
+"""GPU parity of the float-float element operator (bs_apply_A_ff) and of CG
+run with it (BS_CG_FF_OPERATOR) against the FP64 oracle.
+
+Bound: every input is split into a float pair with relative error 2^-48,
+each product of high parts is exact, the cross terms carry a float's 2^-24
+of a 2^-24-sized quantity and TwoSum keeps the high sums exact, so a node's
+error is a small multiple of 2^-46 (|A| |u|)_node, where |A| is the operator
+with every coefficient replaced by its magnitude.  The tests allow 2^-42
+(|A| |u|) elementwise, with |A| assembled densely by the independent numpy
+reference.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_10917_gb300 import bs, synth
+from tests import fem_ref
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("K,N", [(2, 1), (2, 2), (2, 3), (2, 5), (1, 7), (1, 9)])
+@pytest.mark.parametrize("with_coef", [False, True])
+def test_apply_A_ff_within_bound(K, N, with_coef):
+    m = synth.Mesh(K, N, seed=3)
+    lam = 1e-2
+    coef = synth.lognormal(m.E, 5) if with_coef else None
+    Z = bs.Map(m.E, N, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, lam, coef)
+    for scale in (1.0, 1e-20, 1e20):
+        u = synth.uniform(m.NG, 7) * scale
+        got = P.apply_A_ff(cuda(u)).cpu().numpy()
+        want = oracle.apply_A(m.E, N, m.h, lam, m.ids, m.NG, u, coef)
+        A = fem_ref.assemble(m, lam, coef)
+        bound = np.abs(A) @ np.abs(u)
+        assert np.all(np.abs(got - want) <= 2.0 ** -42 * bound)
+        # the FP64 operator, for scale: its one-pass K = D^T W D form and the
+        # oracle's two passes (gradient, then D^T) differ by rounding of
+        # intermediates larger than |A| |u|, a few units of 2^-52 of it
+        g64 = P.apply_A(cuda(u)).cpu().numpy()
+        assert np.all(np.abs(g64 - want) <= 2.0 ** -46 * bound)
+
+
+def test_apply_A_ff_tiny_and_zero_inputs():
+    """Inputs below 2^-102 count as zero in the float-float stiffness; the
+    mass term stays FP64.  A constant vector has no stiffness part (S 1 = 0),
+    so for a tiny constant both operators give the mass alone."""
+    m = synth.Mesh(2, 3, seed=1)
+    Z = bs.Map(m.E, 3, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, 1.0)
+    z = torch.zeros(m.NG, dtype=torch.float64, device="cuda")
+    assert float(P.apply_A_ff(z).abs().max()) == 0.0
+    tiny = torch.full((m.NG,), 2.0 ** -110, dtype=torch.float64, device="cuda")
+    got, want = P.apply_A_ff(tiny), P.apply_A(tiny)
+    assert float(want.abs().min()) > 0.0
+    assert float(((got - want) / want).abs().max()) <= 1e-12
+
+
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_cg_with_ff_operator(jacobi):
+    N, K, lam = 5, 6, 1e-2
+    m = synth.Mesh(K, N, seed=2)
+    coef = synth.lognormal(m.E, 3)
+    Z = bs.Map(m.E, N, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, lam, coef)
+    bh = synth.uniform(m.NG, 11)
+    b = cuda(bh)
+    base = bs.BS_CG_GRAPH | (bs.BS_CG_JACOBI if jacobi else 0)
+    x, info = P.cg(b, tol=1e-8, maxit=20000, flags=base | bs.BS_CG_FF_OPERATOR)
+    x64, i64 = P.cg(b, tol=1e-8, maxit=20000, flags=base)
+    assert info["rc"] == 0
+    assert abs(info["iterations"] - i64["iterations"]) <= max(3, 0.02 * i64["iterations"])
+    r = bh - oracle.apply_A(m.E, N, m.h, lam, m.ids, m.NG, x.cpu().numpy(), coef)
+    assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(bh)
+    assert torch.linalg.norm(x - x64) <= 1e-6 * torch.linalg.norm(x64)
