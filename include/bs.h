@@ -174,7 +174,9 @@ int bs_diag_A(const bs_problem *prob, double *d_diag, void *stream);
  * parts with TwoSum on the FP32 pipes, and only the final combination of a
  * node is FP64.  Error per node: a few units of 2^-46 times sum |K| |u|
  * (about 64 times the FP64 operator's); inputs below 2^-102 in magnitude
- * count as zero.  The gather is the same as bs_apply_A's. */
+ * count as zero (scale b so that the entries that matter lie above that)
+ * and inputs of 2^127 or more become infinite.  The gather is the same as
+ * bs_apply_A's. */
 int bs_apply_A_ff(const bs_problem *prob, const double *p, double *Ap, void *stream);
 
 /* ------------------------------------------------------------ CG */

@@ -170,7 +170,7 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
   for (int i = 0; i < Nq; ++i) {
     tab.w[i] = w[i];
     tabf.w[i] = (float)w[i];
-    tabff.w[i] = w[i];
+    split(w[i], tabff.wh[i], tabff.wl[i]);
     for (int m = 0; m < Nq; ++m) {
       tab.K[i * Nq + m] = K[i * Nq + m];
       tabf.K[i * Nq + m] = (float)K[i * Nq + m];

