@@ -33,50 +33,58 @@ constexpr int kPrepBlock = 256;  // 8 warps, one element per warp
 // One warp per element: u = D^-1 r through the map, rms, the X row as the
 // GEMM operand ([hi] or [hi | hi | lo], padding zero), and rms * oscale to
 // rmsv[e] (0 for an all-zero element).  GB300's FP64 pipe (and the
-// conversions, which share it) runs at 1/64 of the FP32 rate, so each node
-// costs one DMUL (u) and one conversion; the sum of squares and the scaling
-// are FP32.  rms is only a normalisation: the network's output is multiplied
-// back by the same value, so its rounding does not matter.
-constexpr int kPrepMaxPerLane = 32;  // (N+1)^3 <= 1024 nodes per element
-// Row q of X and rmsv belongs to element order[q]: elements visited in the
-// map's order (sorted by smallest global index) meet their neighbours' reads
-// of r and D^-1 in L2, where the random element numbering would not.
+// conversions, which share it) runs at 1/64 of the FP32 rate, so no node
+// touches it: u = D^-1 r is formed in FP32 from the 24-bit high parts of the
+// exact float-pair splits of D^-1 and r (relative error below 2^-22, far
+// under the network's 2^-16), and the sum of squares and the scaling are FP32.
+// rms is only a normalisation: the network's output is multiplied back by the
+// same value, so its rounding does not matter.
+constexpr int kPrepMaxNq = 10;  // degrees up to 9
+template <int NP>
 __global__ void __launch_bounds__(kPrepBlock)
-    k_fp_prep(int64_t E, int Np, int Dp, int split, float oscale,
-              const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
-              const double *__restrict__ r, const double *__restrict__ dinv,
-              __nv_bfloat16 *__restrict__ X, float *__restrict__ rmsv, const CgState *st) {
+    k_fp_prep(int64_t E, int Dp, int split, float oscale, const int32_t *__restrict__ order,
+              const int32_t *__restrict__ ids, const double *__restrict__ r,
+              const double *__restrict__ dinv, __nv_bfloat16 *__restrict__ X,
+              float *__restrict__ rmsv, const CgState *st) {
+  constexpr int T = (NP + 31) / 32;  // nodes per lane
   if (cg_halted(st)) return;
   const int lane = threadIdx.x & 31;
   const int64_t q = (int64_t)blockIdx.x * (kPrepBlock / 32) + (threadIdx.x >> 5);
   if (q >= E) return;
   const int64_t e = order[q];
-  const int32_t *id = ids + e * Np;
-  float uf[kPrepMaxPerLane];
+  const int32_t *id = ids + e * NP;
+  // all of a lane's map entries, then all of its gathers, so that the loads
+  // of an element are in flight together
+  int32_t g[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int l = lane + 32 * t;
+    g[t] = l < NP ? __ldcs(id + l) : -1;
+  }
+  double rv[T], dv[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    rv[t] = g[t] >= 0 ? __ldg(r + g[t]) : 0.0;
+    dv[t] = g[t] >= 0 ? __ldg(dinv + g[t]) : 0.0;
+  }
+  float uf[T];
   float ss = 0.f;
 #pragma unroll
-  for (int t = 0; t < kPrepMaxPerLane; ++t) {
-    const int l = lane + 32 * t;
-    float v = 0.f;
-    if (l < Np) {
-      const int32_t g = __ldcs(id + l);
-      v = g >= 0 ? (float)(__ldg(dinv + g) * __ldg(r + g)) : 0.f;
-    }
-    uf[t] = v;
-    ss = fmaf(v, v, ss);
-    if (32 * (t + 1) >= Np) break;
+  for (int t = 0; t < T; ++t) {
+    uf[t] = ff_split(dv[t]).hi * ff_split(rv[t]).hi;
+    ss = fmaf(uf[t], uf[t], ss);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  const float rms = sqrtf(ss / (float)Np);
+  const float rms = sqrtf(ss / (float)NP);
   const float inv = rms > 0.f ? 1.0f / rms : 0.f;
   __nv_bfloat16 *row = X + q * (split ? 3 * Dp : Dp);
 #pragma unroll
-  for (int t = 0; t < kPrepMaxPerLane; ++t) {
+  for (int t = 0; t < (T > 0 ? T : 1) + 1; ++t) {  // Dp may exceed 32 T by up to 31
     const int l = lane + 32 * t;
     if (l >= Dp) break;
     __nv_bfloat16 hi, lo;
-    bf16_split(l < Np ? uf[t] * inv : 0.f, hi, lo);
+    bf16_split(t < T && l < NP ? uf[t < T ? t : 0] * inv : 0.f, hi, lo);
     row[l] = hi;
     if (split) {
       row[Dp + l] = hi;
@@ -84,6 +92,32 @@ __global__ void __launch_bounds__(kPrepBlock)
     }
   }
   if (lane == 0) rmsv[q] = rms * oscale;
+}
+
+static int launch_fp_prep(int N, int64_t E, int Dp, int split, float oscale, const int32_t *order,
+                          const int32_t *ids, const double *r, const double *dinv,
+                          __nv_bfloat16 *X, float *rmsv, const CgState *st, cudaStream_t s) {
+  const unsigned grid = (unsigned)((E + kPrepBlock / 32 - 1) / (kPrepBlock / 32));
+#define BS_PREP_CASE(NQ)                                                                     \
+  case NQ:                                                                                   \
+    k_fp_prep<NQ * NQ * NQ><<<grid, kPrepBlock, 0, s>>>(E, Dp, split, oscale, order, ids, r, \
+                                                        dinv, X, rmsv, st);                  \
+    break;
+  switch (N + 1) {
+    BS_PREP_CASE(3)
+    BS_PREP_CASE(4)
+    BS_PREP_CASE(5)
+    BS_PREP_CASE(6)
+    BS_PREP_CASE(7)
+    BS_PREP_CASE(8)
+    BS_PREP_CASE(9)
+    BS_PREP_CASE(10)
+    default:
+      return fail(BS_ERR_ARG, "learned FPCG: degree %d outside 2..9", N);
+  }
+#undef BS_PREP_CASE
+  BS_LAUNCH_CHECK();
+  return BS_OK;
 }
 
 // Three-value last-block-done combine (partials holds 3 * gridDim.x).
@@ -141,26 +175,37 @@ __device__ void fpcg_scalars(CgState *st, double rzn, double rzo, double rzj, in
 }
 
 // z' = D^-1 r + corr (have_mlp) or D^-1 r, with the three dot products
-// r.z', r.z_old, r.(D^-1 r); z holds the old z on entry and z' on exit.
+// r.z', r.z_old, r.(D^-1 r); z holds the old z on entry and z' on exit.  z'
+// is one FP64 fused multiply-add per node; the dot products run on the FP32
+// pipes as float-pair sums of exact float-pair splits (error a few units of
+// 2^-46 of the sum of |terms|), so the kernel is bound by HBM, not by
+// GB300's narrow FP64 pipe.
 __global__ void __launch_bounds__(kReduceBlock)
     k_fpcg_z(int64_t NG, const double *__restrict__ r, const double *__restrict__ dinv,
              const double *__restrict__ corr, double *__restrict__ z, double *partials,
              unsigned int *counter, CgState *st, int init, int have_mlp) {
   if (cg_halted(st)) return;
-  double an = 0.0, ao = 0.0, aj = 0.0;
+  FF an{0.f, 0.f}, ao{0.f, 0.f}, aj{0.f, 0.f};
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = tid; g < NG; g += nth) {
-    const double rg = r[g], zj = dinv[g] * rg;
-    const double zn = have_mlp ? zj + corr[g] : zj;
-    if (!init) ao = fma(rg, z[g], ao);
-    an = fma(rg, zn, an);
-    aj = fma(rg, zj, aj);
+    const double rg = r[g], dg = dinv[g];
+    const double zn = have_mlp ? fma(dg, rg, corr[g]) : dg * rg;
+    const FF rs = ff_split(rg), ds = ff_split(dg), zs = ff_split(zn);
+    if (!init) {
+      const FF zo = ff_split(z[g]);
+      ff_fma(ao, rs.hi, rs.lo, zo.hi, zo.lo);
+    }
+    ff_fma(an, rs.hi, rs.lo, zs.hi, zs.lo);
+    // r (D^-1 r): the product D^-1 r as an unevaluated pair, then times r
+    FF j{0.f, 0.f};
+    ff_fma(j, ds.hi, ds.lo, rs.hi, rs.lo);
+    ff_fma(aj, j.hi, j.lo, rs.hi, rs.lo);
     z[g] = zn;
   }
-  const double pn = block_sum<kReduceBlock>(an);
-  const double po = block_sum<kReduceBlock>(ao);
-  const double pj = block_sum<kReduceBlock>(aj);
+  const double pn = block_sum<kReduceBlock>(ff_widen(an.hi) + ff_widen(an.lo));
+  const double po = block_sum<kReduceBlock>(ff_widen(ao.hi) + ff_widen(ao.lo));
+  const double pj = block_sum<kReduceBlock>(ff_widen(aj.hi) + ff_widen(aj.lo));
   double tn, to, tj;
   if (grid_combine3<kReduceBlock>(pn, po, pj, partials, counter, &tn, &to, &tj) &&
       threadIdx.x == 0)
@@ -259,10 +304,9 @@ static int precondition(const bs_problem *P, bs_mlp *mlp, int odd, int init, cud
   if (mlp) {
     const int64_t E = m->E;
     float *rmsv = mlp->Y;  // E floats of inference scratch
-    k_fp_prep<<<(unsigned)((E + 7) / 8), kPrepBlock, 0, s>>>(E, Np, mlp->Dp, mlp->split, 1.0f,
-                                                            m->d_elem_order, m->d_ids, v.r,
-                                                            v.dinv, mlp->Xb, rmsv, st);
-    BS_LAUNCH_CHECK();
+    if (int rc = launch_fp_prep(P->N, E, mlp->Dp, mlp->split, 1.0f, m->d_elem_order, m->d_ids,
+                                v.r, v.dinv, mlp->Xb, rmsv, st, s))
+      return rc;
     GemmArgs b{};
     b.nvalid = mlp->nI;
     b.out_f64 = v.corr;
@@ -559,7 +603,7 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
   if (mlp) {
     BS_ARG(mlp->device == dev, "bs_fpcg_learned: mlp on another device");
     BS_ARG(mlp->D == Np, "bs_fpcg_learned: mlp input size %d != (N+1)^3 = %d", mlp->D, Np);
-    BS_ARG(Np <= 32 * kPrepMaxPerLane, "bs_fpcg_learned: degree %d above 9", P->N);
+    BS_ARG(P->N + 1 <= kPrepMaxNq, "bs_fpcg_learned: degree %d above 9", P->N);
     if (int rc = mlp_ensure(mlp, m->E > 32 ? m->E : 32)) return rc;
     BS_ARG(mlp->nI > 0, "bs_fpcg_learned: the network needs N >= 2 (element-interior outputs)");
     if (int rc = mlp_interior_operand(mlp, odd, as_stream(stream))) return rc;
