@@ -242,13 +242,16 @@ int bs_cg_solve_refined_f32(const bs_problem *prob, const double *b, double *x,
  * device from per-item partial sums taken in a fixed order (deterministic).
  * Solves that have stopped drop out of the work lists at no cost.
  *  - probs[s] must be distinct problems on the current device (each lends its
- *    scratch); b[s], x[s] are DEVICE vectors of its N_G; x0 = 0.
+ *    scratch), of degree N <= 8; b[s], x[s] are DEVICE vectors of its N_G;
+ *    x0 = 0.
  *  - Stop: r.r <= tol^2 b.b per solve, or maxit iterations.
  *  - flags: BS_CG_GRAPH (iterations replayed as a CUDA graph),
  *    BS_CG_REFINED_F32 (FP32-storage inner CG of every solve inside an FP64
  *    iterative refinement done for all solves together; inner tolerance 1e-4,
  *    at most 50 refinement steps; then tol is met by the FP64 TRUE residual
- *    and maxit caps each solve's total inner iterations).
+ *    and maxit caps each solve's total inner iterations), or
+ *    BS_CG_FF_OPERATOR (FP64 form with the float-float element operator of
+ *    bs_apply_A_ff).
  *  - infos[s] (host, may be NULL) receives each solve's iterations, outer
  *    steps, final r.r, b.b, relative residual, status; seconds is the whole
  *    batch's wall time.  Synchronises `stream`.
@@ -258,6 +261,42 @@ int bs_cg_solve_batched(int32_t nsolves, const bs_problem *const *probs,
                         const double *const *b, double *const *x, double tol,
                         int32_t maxit, int32_t flags, bs_cg_info *infos,
                         void *stream);
+
+/* Launch configuration of the batched solver.  Every field 0 = default.
+ *  chunk: vector entries per work item of the update phases (a power of two
+ *         in [1024, 65536]; default 4096);
+ *  blocks_per_sm: cooperative grid = SMs x this, capped by occupancy
+ *         (default: the occupancy maximum);
+ *  unroll: vector entries each thread carries per sweep of the update
+ *         phases, all loads issued together (1, 2, 4 or 8; default 4).
+ * The block size (256 threads) is fixed by the element operator's mapping.
+ * chunk and unroll change the order of the per-solve sums (results differ in
+ * rounding, not in convergence); blocks_per_sm does not.  A given
+ * configuration is deterministic. */
+typedef struct {
+  int32_t chunk;
+  int32_t blocks_per_sm;
+  int32_t unroll;
+} bs_batched_config;
+
+/* bs_cg_solve_batched with an explicit configuration (cfg may be NULL). */
+int bs_cg_solve_batched_ex(int32_t nsolves, const bs_problem *const *probs,
+                           const double *const *b, double *const *x, double tol,
+                           int32_t maxit, int32_t flags, const bs_batched_config *cfg,
+                           bs_cg_info *infos, void *stream);
+
+/* Autotuner: times `iters` batched iterations (after one untimed) of these
+ * solves under each candidate configuration -- chunk in {2048, 4096, 8192,
+ * 16384} x unroll in {2, 4, 8} x blocks_per_sm in {1, occupancy maximum} --
+ * from x = 0 into scratch solution vectors it allocates (the problems'
+ * scratch is overwritten), with the given flags (BS_CG_REFINED_F32 times the
+ * FP32 inner iteration, BS_CG_FF_OPERATOR the float-float one), and writes
+ * the fastest to *best and its time per iteration (ms) to
+ * *ms_per_iteration (may be NULL).  Synchronises `stream`. */
+int bs_cg_batched_autotune(int32_t nsolves, const bs_problem *const *probs,
+                           const double *const *b, int32_t flags, int32_t iters,
+                           bs_batched_config *best, double *ms_per_iteration,
+                           void *stream);
 
 /* ------------------------------------------------------------ learned preconditioner */
 

@@ -356,23 +356,72 @@ class Problem:
         return x, d
 
 
-def solve_batched(problems, bs_, xs, tol=1e-8, maxit=1000000, flags=0, check=True):
-    """bs_cg_solve_batched: Algorithm 1 on every (problem, b, x) together.
-    Returns (rc, list of per-solve info dicts)."""
+class BatchedConfig(ctypes.Structure):
+    """bs_batched_config: chunk, blocks_per_sm, unroll (0 = default)."""
+    _fields_ = [("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("unroll", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_SIGS.update({
+    "bs_cg_solve_batched_ex": (ctypes.c_int, [_i32, _vp, _vp, _vp, _d, _i32, _i32,
+                                              ctypes.POINTER(BatchedConfig),
+                                              ctypes.POINTER(CgInfo), _vp]),
+    "bs_cg_batched_autotune": (ctypes.c_int, [_i32, _vp, _vp, _i32, _i32,
+                                              ctypes.POINTER(BatchedConfig),
+                                              ctypes.POINTER(_d), _vp]),
+})
+
+
+def _arrays(problems, bs_, xs=None):
     n = len(problems)
-    if not (n == len(bs_) == len(xs)) or n == 0:
+    if n == 0 or n != len(bs_) or (xs is not None and n != len(xs)):
         raise ValueError("problems, b and x must be non-empty lists of one length")
     P = (ctypes.c_void_p * n)(*[p.handle.value for p in problems])
     B = (ctypes.c_void_p * n)(*[_ptr(b, name="b").value for b in bs_])
-    X = (ctypes.c_void_p * n)(*[_ptr(x, name="x").value for x in xs])
+    X = None if xs is None else (ctypes.c_void_p * n)(*[_ptr(x, name="x").value for x in xs])
+    return n, P, B, X
+
+
+def solve_batched(problems, bs_, xs, tol=1e-8, maxit=1000000, flags=0, check=True, config=None):
+    """bs_cg_solve_batched(_ex): Algorithm 1 on every (problem, b, x) together;
+    config: a BatchedConfig or a dict of its fields (None: defaults).
+    Returns (rc, list of per-solve info dicts)."""
+    n, P, B, X = _arrays(problems, bs_, xs)
     infos = (CgInfo * n)()
-    rc = lib().bs_cg_solve_batched(n, ctypes.cast(P, ctypes.c_void_p),
+    cfg = None
+    if config is not None:
+        cfg = config if isinstance(config, BatchedConfig) else BatchedConfig(**config)
+    L = lib()
+    if cfg is None:
+        rc = L.bs_cg_solve_batched(n, ctypes.cast(P, ctypes.c_void_p),
                                    ctypes.cast(B, ctypes.c_void_p),
                                    ctypes.cast(X, ctypes.c_void_p), tol, maxit, flags, infos,
                                    _stream())
+    else:
+        _bind(["bs_cg_solve_batched_ex"])
+        rc = L.bs_cg_solve_batched_ex(n, ctypes.cast(P, ctypes.c_void_p),
+                                      ctypes.cast(B, ctypes.c_void_p),
+                                      ctypes.cast(X, ctypes.c_void_p), tol, maxit, flags,
+                                      ctypes.byref(cfg), infos, _stream())
     if check and rc != BS_OK:
         _check(rc, "bs_cg_solve_batched")
     return rc, [infos[i].as_dict() for i in range(n)]
+
+
+def autotune_batched(problems, bs_, flags=0, iters=4):
+    """bs_cg_batched_autotune: returns (BatchedConfig, ms per iteration)."""
+    n, P, B, _ = _arrays(problems, bs_)
+    L = _bind(["bs_cg_batched_autotune"])
+    best = BatchedConfig()
+    ms = ctypes.c_double(0.0)
+    _check(L.bs_cg_batched_autotune(n, ctypes.cast(P, ctypes.c_void_p),
+                                    ctypes.cast(B, ctypes.c_void_p), flags, iters,
+                                    ctypes.byref(best), ctypes.byref(ms), _stream()),
+           "bs_cg_batched_autotune")
+    return best, ms.value
 
 
 # ---------------------------------------------------------------- learned preconditioner

@@ -27,14 +27,14 @@
 #include <cstring>
 #include <vector>
 
-#include "bs_op.cuh"
+#include "bs_op_ff.cuh"
 
 namespace bs {
 
 constexpr int kBBlock = 256;
 constexpr int kBMaxNq = 9;                       // degrees 1..8 in a batch
 constexpr int kBSmem = 2187;                     // max EPB * Nq^3 for Nq <= 9 (>= kTileNnz)
-constexpr int kBChunk = 4096;                    // vector entries per C/D item
+constexpr int kBChunk = 4096;                    // default vector entries per C/D item
 constexpr long long kBarrierBudget = 1ll << 32;  // clock cycles (~2 s) per barrier wait
 
 struct BDesc {
@@ -46,6 +46,8 @@ struct BDesc {
   const double *coef;
   const OpTab<double> *tab;
   const OpTab<float> *tabf;
+  const OpTabFF *tabff;
+  int ff;  // FP64 form: the float-float element operator
   double g, mlam;
   double *x, *r, *p, *Ap, *ApL;  // FP64 (x: the solution)
   const double *b;
@@ -126,9 +128,46 @@ __device__ __noinline__ void ax_call(int64_t slot0, int64_t E, const int32_t *or
                                 s_w);
 }
 
-// Element operator on one item (block-uniform dispatch on the degree).
-template <typename T, bool GATHER_IN>
+// The float-float element operator (bs_op_ff.cuh) as a real call.
+template <int NQ>
+__device__ __noinline__ void ax_call_ff(int64_t slot0, int64_t E, const int32_t *order,
+                                        const int32_t *ids, const double *in, double *out,
+                                        const OpTabFF *tab, const double *coef, double g,
+                                        double mlam, float *smem) {
+  float *s_uh = smem, *s_ul = smem + kBSmem, *s_K = smem + 2 * kBSmem;
+  float *s_w = s_K + 4 * kBMaxNq * kBMaxNq;
+  ax_elements_ff<NQ, true>(slot0, E, order, ids, in, out, tab, coef, g, mlam, s_uh, s_ul, s_K,
+                           s_w);
+}
+
+// Element operator on one item (block-uniform dispatch on the degree); FF:
+// the float-float operator (FP64 form only).
+template <typename T, bool GATHER_IN, bool FF = false>
 __device__ void item_ax(const BDesc &d, int64_t slot0, const T *in, T *out, T *smem) {
+  if constexpr (FF) {
+    static_assert(sizeof(T) == 8 && GATHER_IN, "float-float operator: FP64 form only");
+    {
+      float *fs = reinterpret_cast<float *>(smem);
+#define BS_BF_CASE(NQ)                                                                        \
+  case NQ:                                                                                    \
+    ax_call_ff<NQ>(slot0, d.E, d.order, d.ids, (const double *)in, (double *)out, d.tabff,    \
+                   d.coef, d.g, d.mlam, fs);                                                  \
+    return;
+      switch (d.NQ) {
+        BS_BF_CASE(2)
+        BS_BF_CASE(3)
+        BS_BF_CASE(4)
+        BS_BF_CASE(5)
+        BS_BF_CASE(6)
+        BS_BF_CASE(7)
+        BS_BF_CASE(8)
+        BS_BF_CASE(9)
+        default:
+          return;
+      }
+#undef BS_BF_CASE
+    }
+  } else {
   T *s_K = smem + kBSmem;
   T *s_w = s_K + kBMaxNq * kBMaxNq;
   const T g = (T)d.g, mlam = (T)d.mlam;
@@ -151,6 +190,7 @@ __device__ void item_ax(const BDesc &d, int64_t slot0, const T *in, T *out, T *s
       break;
   }
 #undef BS_B_CASE
+  }
 }
 
 // Sum of part[a..b) in a fixed order over the block (valid in thread 0).
@@ -183,6 +223,7 @@ __device__ bool item_done(double part, double *parts, int item, int first, int l
 
 struct BLists {
   const BDesc *d;
+  int chunk;                  // vector entries per C/D item
   const int2 *iA, *iB, *iC;
   int nA, nB, nC;
   const int4 *rng;            // [nsolves] (b0, b1, c0, c1): item ranges in lists B and C
@@ -218,17 +259,27 @@ __device__ void finish_iteration(const BLists &L, int s, CgState *st, double rr_
   if (done) stop_solve(L, s, st, done);
 }
 
-// One CG iteration of every running solve (cooperative launch).
-template <typename T>
-__global__ void __launch_bounds__(kBBlock, sizeof(T) == 8 ? 2 : 4) k_batched_iter(BLists L) {
-  __shared__ __align__(16) T smem[kBSmem + kBMaxNq * kBMaxNq + 16];
+// Shared memory of the element phase, in T: the element values, K and w
+// (FP64 / FP32 operator), or, viewed as floats, the float pairs of the
+// values, the four split tables and the split weights (float-float
+// operator).
+constexpr int kBSmemD = kBSmem + 2 * kBMaxNq * kBMaxNq + 32;
+
+// One CG iteration of every running solve (cooperative launch).  U: vector
+// entries per thread per sweep in the update phases (a tuning parameter);
+// FF: the float-float element operator, which needs fewer registers, so
+// that variant runs three blocks per SM instead of two.
+template <typename T, int U, bool FF>
+__global__ void __launch_bounds__(kBBlock, FF ? 3 : (sizeof(T) == 8 ? 2 : 4))
+    k_batched_iter(BLists L) {
+  __shared__ __align__(16) T smem[sizeof(T) == 8 ? kBSmemD : kBSmem + kBMaxNq * kBMaxNq + 16];
   if (*(volatile int *)L.err) return;
   // A: ApL = A_L (Z p)
   for (int it = blockIdx.x; it < L.nA; it += gridDim.x) {
     const int2 w = L.iA[it];
     const BDesc &d = L.d[w.x];
     if (solve_off(d)) continue;
-    item_ax<T, true>(d, w.y, BV<T>::p(d), BV<T>::ApL(d), smem);
+    item_ax<T, true, FF>(d, w.y, BV<T>::p(d), BV<T>::ApL(d), smem);
   }
   if (!grid_sync(L.bar, L.err)) return;
   // B: Ap = Z^T ApL; p.Ap -> alpha
@@ -263,14 +314,14 @@ __global__ void __launch_bounds__(kBBlock, sizeof(T) == 8 ? 2 : 4) k_batched_ite
     const T a = BV<T>::alpha(d.st), na = -a;
     T *x = BV<T>::x(d), *r = BV<T>::r(d);
     const T *p = BV<T>::p(d), *Ap = BV<T>::Ap(d);
-    const int64_t i0 = (int64_t)w.y * kBChunk;
-    const int64_t i1 = i0 + kBChunk < d.NG ? i0 + kBChunk : d.NG;
+    const int64_t i0 = (int64_t)w.y * L.chunk;
+    const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
     Acc<T> acc;
-    // four entries per thread per sweep, all sixteen loads issued together
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += 4 * kBBlock) {
-      T pv[4], av[4], xv[4], rv[4];
+    // U entries per thread per sweep, all 4 U loads issued together
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += U * kBBlock) {
+      T pv[U], av[U], xv[U], rv[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int64_t k = i + u * kBBlock;
         const bool in = k < i1;
         pv[u] = in ? p[k] : T(0);
@@ -279,7 +330,7 @@ __global__ void __launch_bounds__(kBBlock, sizeof(T) == 8 ? 2 : 4) k_batched_ite
         rv[u] = in ? r[k] : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int64_t k = i + u * kBBlock;
         if (k < i1) {
           x[k] = fmaT(a, pv[u], xv[u]);
@@ -304,18 +355,18 @@ __global__ void __launch_bounds__(kBBlock, sizeof(T) == 8 ? 2 : 4) k_batched_ite
     const T bt = BV<T>::beta(d.st);
     T *p = BV<T>::p(d);
     const T *r = BV<T>::r(d);
-    const int64_t i0 = (int64_t)w.y * kBChunk;
-    const int64_t i1 = i0 + kBChunk < d.NG ? i0 + kBChunk : d.NG;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += 4 * kBBlock) {
-      T rv[4], pv[4];
+    const int64_t i0 = (int64_t)w.y * L.chunk;
+    const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += U * kBBlock) {
+      T rv[U], pv[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int64_t k = i + u * kBBlock;
         rv[u] = k < i1 ? r[k] : T(0);
         pv[u] = k < i1 ? p[k] : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int64_t k = i + u * kBBlock;
         if (k < i1) p[k] = fmaT(T(1), rv[u], bt * pv[u]);
       }
@@ -328,8 +379,8 @@ __global__ void __launch_bounds__(kBBlock) k_batched_start(BLists L, double tol2
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
     const BDesc &d = L.d[w.x];
-    const int64_t i0 = (int64_t)w.y * kBChunk;
-    const int64_t i1 = i0 + kBChunk < d.NG ? i0 + kBChunk : d.NG;
+    const int64_t i0 = (int64_t)w.y * L.chunk;
+    const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
     Acc<double> acc;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kBBlock) {
       const double bi = d.b[i];
@@ -360,7 +411,7 @@ __global__ void __launch_bounds__(kBBlock) k_batched_start(BLists L, double tol2
 // Refined form, FP64 outer residual, phase 1: ApL = A_L (Z x) for solves
 // that have not converged (x64 through the map, FP64 element operator).
 __global__ void __launch_bounds__(kBBlock) k_batched_outer_ax(BLists L) {
-  __shared__ __align__(16) double smem[kBSmem + kBMaxNq * kBMaxNq + 16];
+  __shared__ __align__(16) double smem[kBSmemD];
   for (int it = blockIdx.x; it < L.nA; it += gridDim.x) {
     const int2 w = L.iA[it];
     const BDesc &d = L.d[w.x];
@@ -392,8 +443,8 @@ __global__ void __launch_bounds__(kBBlock)
     const int2 w = L.iC[it];
     BDesc &d = D[w.x];
     if (d.outer_done) continue;
-    const int64_t i0 = (int64_t)w.y * kBChunk;
-    const int64_t i1 = i0 + kBChunk < d.NG ? i0 + kBChunk : d.NG;
+    const int64_t i0 = (int64_t)w.y * L.chunk;
+    const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
     Acc<double> acc;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kBBlock) {
       const double ri = d.b[i] - d.Ap[i];
@@ -440,8 +491,8 @@ __global__ void __launch_bounds__(kBBlock) k_batched_outer_update(BDesc *D, BLis
     const int2 w = L.iC[it];
     BDesc &d = D[w.x];
     if (!d.active) continue;
-    const int64_t i0 = (int64_t)w.y * kBChunk;
-    const int64_t i1 = i0 + kBChunk < d.NG ? i0 + kBChunk : d.NG;
+    const int64_t i0 = (int64_t)w.y * L.chunk;
+    const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kBBlock) d.x[i] = d.x[i] + (double)d.df[i];
     if (w.y == 0 && threadIdx.x == 0) d.outer += 1;
   }
@@ -454,8 +505,8 @@ __global__ void k_batched_zero_x(BLists L) {
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
     const BDesc &d = L.d[w.x];
-    const int64_t i0 = (int64_t)w.y * kBChunk;
-    const int64_t i1 = i0 + kBChunk < d.NG ? i0 + kBChunk : d.NG;
+    const int64_t i0 = (int64_t)w.y * L.chunk;
+    const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kBBlock) d.x[i] = 0.0;
   }
 }
@@ -465,8 +516,8 @@ __global__ void __launch_bounds__(kBBlock) k_batched_bb(BDesc *D, BLists L) {
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
     BDesc &d = D[w.x];
-    const int64_t i0 = (int64_t)w.y * kBChunk;
-    const int64_t i1 = i0 + kBChunk < d.NG ? i0 + kBChunk : d.NG;
+    const int64_t i0 = (int64_t)w.y * L.chunk;
+    const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
     Acc<double> acc;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += kBBlock) acc.add(d.b[i], d.b[i]);
     const double part = block_sum<kBBlock>(acc.value());
@@ -498,6 +549,8 @@ struct Batch {
   std::vector<int> members;       // solves in the current lists
   BLists L{};
   int grid_iter = 0;
+  int chunk = kBChunk, unroll = 4;  // tuning parameters (bs_batched_config)
+  bool ff = false;                   // FP64 form with the float-float operator
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
   ~Batch() {
@@ -560,7 +613,7 @@ static int read_flags(Batch &B, cudaStream_t s) {
 }
 
 static int build_batch(Batch &B, int ns, const bs_problem *const *P, const double *const *b,
-                       double *const *x, bool f32) {
+                       double *const *x, bool f32, bool ff) {
   B.ns = ns;
   std::vector<BDesc> desc((size_t)ns);
   B.hA.assign((size_t)ns, {});
@@ -583,6 +636,8 @@ static int build_batch(Batch &B, int ns, const bs_problem *const *P, const doubl
     d.coef = p->d_coef;
     d.tab = p->d_tab;
     d.tabf = p->d_tabf;
+    d.tabff = p->d_tabff;
+    d.ff = ff ? 1 : 0;
     d.g = 0.5 * p->h;
     d.mlam = p->lambda * d.g * d.g * d.g;
     const int64_t sv = m->NG + 2;
@@ -605,7 +660,7 @@ static int build_batch(Batch &B, int ns, const bs_problem *const *P, const doubl
     const int epb = nq2 >= 128 ? 1 : 256 / nq2;
     for (int64_t e = 0; e < m->E; e += epb) B.hA[(size_t)s].push_back(make_int2(s, (int)e));
     for (int64_t t = 0; t < m->ntiles; ++t) B.hB[(size_t)s].push_back(make_int2(s, (int)t));
-    const int64_t nch = (m->NG + kBChunk - 1) / kBChunk;
+    const int64_t nch = (m->NG + B.chunk - 1) / B.chunk;
     for (int64_t c = 0; c < (nch > 0 ? nch : 1); ++c)
       B.hC[(size_t)s].push_back(make_int2(s, (int)c));
     B.capA += B.hA[(size_t)s].size();
@@ -625,6 +680,7 @@ static int build_batch(Batch &B, int ns, const bs_problem *const *P, const doubl
   BS_CUDA_TRY(cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking));
   BLists &L = B.L;
   L.d = B.d_desc;
+  L.chunk = B.chunk;
   L.iA = B.d_items;
   L.iB = B.d_items + B.capA;
   L.iC = B.d_items + B.capA + B.capB;
@@ -643,6 +699,24 @@ static int build_batch(Batch &B, int ns, const bs_problem *const *P, const doubl
   return upload_lists(B, all, nullptr);
 }
 
+template <typename T, bool FF>
+static void *iter_kernel_ff(int unroll) {
+  switch (unroll) {
+    case 1: return (void *)k_batched_iter<T, 1, FF>;
+    case 2: return (void *)k_batched_iter<T, 2, FF>;
+    case 8: return (void *)k_batched_iter<T, 8, FF>;
+    default: return (void *)k_batched_iter<T, 4, FF>;
+  }
+}
+
+template <typename T>
+static void *iter_kernel(int unroll, bool ff = false) {
+  if constexpr (sizeof(T) == 8) {
+    if (ff) return iter_kernel_ff<double, true>(unroll);
+  }
+  return iter_kernel_ff<T, false>(unroll);
+}
+
 template <typename T>
 static int launch_iter(Batch &B, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -655,7 +729,8 @@ static int launch_iter(Batch &B, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_batched_iter<T>, B.L));
+  void *args[] = {&B.L};
+  BS_CUDA_TRY(cudaLaunchKernelExC(&cfg, iter_kernel<T>(B.unroll, B.ff), args));
   return BS_OK;
 }
 
@@ -704,56 +779,91 @@ static int iterate(Batch &B, bool graph, int maxit, cudaStream_t s) {
   return BS_OK;
 }
 
-template <typename K>
-static int occupancy_grid(K kern) {
+// Cooperative grid: SMs x blocks per SM, the occupancy maximum or fewer
+// (want > 0).
+static int occupancy_grid(const void *kern, int want = 0) {
   DeviceInfo di;
   if (device_info(&di)) return 0;
   int bps = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kBBlock, 0) != cudaSuccess ||
       bps < 1)
     return 0;
+  if (want > 0 && want < bps) bps = want;
   return bps * di.sms;
 }
 
 }  // namespace bs
 
-using namespace bs;
+namespace bs {
 
-extern "C" int bs_cg_solve_batched(int32_t nsolves, const bs_problem *const *probs,
-                                   const double *const *b, double *const *x, double tol,
-                                   int32_t maxit, int32_t flags, bs_cg_info *infos,
-                                   void *stream) {
-  const auto t0 = std::chrono::steady_clock::now();
-  BS_ARG(nsolves >= 1 && probs && b && x, "bs_cg_solve_batched: empty or NULL arguments");
-  BS_ARG(maxit >= 0, "bs_cg_solve_batched: maxit < 0");
-  BS_ARG(tol >= 0.0 && std::isfinite(tol), "bs_cg_solve_batched: bad tol");
-  BS_ARG(!(flags & (BS_CG_JACOBI | BS_CG_FIXED_ITERS | BS_CG_X0)),
-         "bs_cg_solve_batched: only BS_CG_GRAPH and BS_CG_REFINED_F32 are supported");
+// Validates the arguments and prepares the FP32 scratch of the refined form.
+static int check_batch(int32_t nsolves, const bs_problem *const *probs, const double *const *b,
+                       double *const *x, double tol, int32_t maxit, int32_t flags,
+                       const bs_batched_config *cfg, const char *fn) {
+  BS_ARG(nsolves >= 1 && probs && b, "%s: empty or NULL arguments", fn);
+  BS_ARG(maxit >= 0, "%s: maxit < 0", fn);
+  BS_ARG(tol >= 0.0 && std::isfinite(tol), "%s: bad tol", fn);
+  BS_ARG(!(flags & ~(BS_CG_GRAPH | BS_CG_REFINED_F32 | BS_CG_FF_OPERATOR)),
+         "%s: only BS_CG_GRAPH, BS_CG_REFINED_F32 and BS_CG_FF_OPERATOR are supported", fn);
+  BS_ARG(!((flags & BS_CG_REFINED_F32) && (flags & BS_CG_FF_OPERATOR)),
+         "%s: BS_CG_FF_OPERATOR applies to the FP64 form only", fn);
+  if (cfg) {
+    const int c = cfg->chunk, u = cfg->unroll;
+    BS_ARG(c == 0 || (c >= 1024 && c <= 65536 && (c & (c - 1)) == 0),
+           "%s: chunk %d is not 0 or a power of two in [1024, 65536]", fn, c);
+    BS_ARG(u == 0 || u == 1 || u == 2 || u == 4 || u == 8, "%s: unroll %d not in {1,2,4,8}", fn,
+           u);
+    BS_ARG(cfg->blocks_per_sm >= 0, "%s: blocks_per_sm < 0", fn);
+  }
   const bool f32 = flags & BS_CG_REFINED_F32;
   int dev = -1;
   BS_CUDA_TRY(cudaGetDevice(&dev));
   for (int s = 0; s < nsolves; ++s) {
-    BS_ARG(probs[s] && b[s] && x[s], "bs_cg_solve_batched: NULL entry %d", s);
-    BS_ARG(probs[s]->device == dev, "bs_cg_solve_batched: problem %d on another device", s);
-    BS_ARG(probs[s]->N + 1 <= kBMaxNq, "bs_cg_solve_batched: problem %d has degree %d > %d",
-           s, probs[s]->N, kBMaxNq - 1);
-    BS_ARG(probs[s]->map->NG > 0, "bs_cg_solve_batched: problem %d is empty", s);
-    for (int t = 0; t < s; ++t)
-      BS_ARG(probs[t] != probs[s], "bs_cg_solve_batched: problem %d repeats %d", s, t);
+    BS_ARG(probs[s] && b[s] && (!x || x[s]), "%s: NULL entry %d", fn, s);
+    BS_ARG(probs[s]->device == dev, "%s: problem %d on another device", fn, s);
+    BS_ARG(probs[s]->N + 1 <= kBMaxNq, "%s: problem %d has degree %d > %d", fn, s, probs[s]->N,
+           kBMaxNq - 1);
+    BS_ARG(probs[s]->map->NG > 0, "%s: problem %d is empty", fn, s);
+    for (int t = 0; t < s; ++t) BS_ARG(probs[t] != probs[s], "%s: problem %d repeats %d", fn, s, t);
     if (f32 && !probs[s]->d_f32) {
       bs_problem *p = const_cast<bs_problem *>(probs[s]);
       BS_CUDA_TRY(cudaMalloc(&p->d_f32, sizeof(float) * 4 * ((size_t)p->map->NG + 8)));
     }
   }
+  return BS_OK;
+}
+
+// Sets up a batch with the given configuration (chunk, unroll, grid).
+static int setup_batch(Batch &B, int32_t nsolves, const bs_problem *const *probs,
+                       const double *const *b, double *const *x, int32_t flags,
+                       const bs_batched_config *cfg) {
+  const bool f32 = flags & BS_CG_REFINED_F32;
+  if (cfg && cfg->chunk) B.chunk = cfg->chunk;
+  if (cfg && cfg->unroll) B.unroll = cfg->unroll;
+  B.ff = flags & BS_CG_FF_OPERATOR;
+  if (int rc = build_batch(B, nsolves, probs, b, x, f32, B.ff)) return rc;
+  B.grid_iter = occupancy_grid(f32 ? iter_kernel<float>(B.unroll)
+                                   : iter_kernel<double>(B.unroll, B.ff),
+                               cfg ? cfg->blocks_per_sm : 0);
+  if (B.grid_iter < 1) return fail(BS_ERR_CUDA, "batched CG: no cooperative grid");
+  return BS_OK;
+}
+
+static int solve_batched(int32_t nsolves, const bs_problem *const *probs, const double *const *b,
+                         double *const *x, double tol, int32_t maxit, int32_t flags,
+                         const bs_batched_config *cfg, bs_cg_info *infos, void *stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  BS_ARG(x != nullptr, "bs_cg_solve_batched: x is NULL");
+  if (int rc = check_batch(nsolves, probs, b, x, tol, maxit, flags, cfg, "bs_cg_solve_batched"))
+    return rc;
+  const bool f32 = flags & BS_CG_REFINED_F32;
   cudaStream_t s = as_stream(stream);
   Batch B;
-  int rc = build_batch(B, nsolves, probs, b, x, f32);
+  int rc = setup_batch(B, nsolves, probs, b, x, flags, cfg);
   if (rc) return rc;
-  B.grid_iter = f32 ? occupancy_grid(k_batched_iter<float>) : occupancy_grid(k_batched_iter<double>);
-  if (B.grid_iter < 1) return fail(BS_ERR_CUDA, "bs_cg_solve_batched: no cooperative grid");
   const bool graph = flags & BS_CG_GRAPH;
   const int G = stream_grid((int64_t)B.capC, 1, 1, 8);
-  const int GA = occupancy_grid(k_batched_outer_ax);
+  const int GA = occupancy_grid((const void *)k_batched_outer_ax);
   if (!f32) {
     k_batched_start<<<G, kBBlock, 0, s>>>(B.L, tol * tol, maxit);
     BS_LAUNCH_CHECK();
@@ -835,3 +945,105 @@ extern "C" int bs_cg_solve_batched(int32_t nsolves, const bs_problem *const *pro
   if (worst && !rc) return fail(worst, "bs_cg_solve_batched: some solves did not converge");
   return rc;
 }
+
+// Candidates: chunk x unroll x blocks per SM; each runs `iters` iterations
+// (after one untimed) of the real solves from x = 0 into scratch solution
+// vectors, timed with CUDA events; the fastest wins.
+static int autotune(int32_t nsolves, const bs_problem *const *probs, const double *const *b,
+                    int32_t flags, int32_t iters, bs_batched_config *best, double *best_ms,
+                    void *stream) {
+  if (int rc = check_batch(nsolves, probs, b, nullptr, 0.0, 1 << 30, flags, nullptr,
+                           "bs_cg_batched_autotune"))
+    return rc;
+  BS_ARG(best != nullptr && iters >= 1, "bs_cg_batched_autotune: NULL best or iters < 1");
+  const bool f32 = flags & BS_CG_REFINED_F32;
+  cudaStream_t s = as_stream(stream);
+  std::vector<double *> xs((size_t)nsolves, nullptr);
+  int rc = BS_OK;
+  for (int i = 0; i < nsolves && !rc; ++i)
+    if (cudaMalloc(&xs[(size_t)i], sizeof(double) * (size_t)probs[i]->map->NG) != cudaSuccess)
+      rc = fail(BS_ERR_ALLOC, "bs_cg_batched_autotune: scratch solution %d", i);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(BS_ERR_CUDA, "bs_cg_batched_autotune: events");
+  double bestv = INFINITY;
+  const int chunks[] = {2048, 4096, 8192, 16384};
+  const int unrolls[] = {2, 4, 8};
+  const int bpss[] = {1, 0};
+  for (int c : chunks)
+    for (int u : unrolls)
+      for (int bp : bpss) {
+        if (rc) break;
+        bs_batched_config cfg{c, bp, u};
+        Batch B;
+        if ((rc = setup_batch(B, nsolves, probs, b, xs.data(), flags, &cfg))) break;
+        const int G = stream_grid((int64_t)B.capC, 1, 1, 8);
+        if (!f32) {
+          k_batched_start<<<G, kBBlock, 0, s>>>(B.L, 0.0, 1 << 30);
+        } else {
+          // the first inner solve of the refined form: r = b (x = 0)
+          k_batched_zero_x<<<G, kBBlock, 0, s>>>(B.L);
+          k_batched_bb<<<G, kBBlock, 0, s>>>(B.d_desc, B.L);
+          const int GA = occupancy_grid((const void *)k_batched_outer_ax);
+          k_batched_outer_ax<<<GA > 0 ? GA : G, kBBlock, 0, s>>>(B.L);
+          k_batched_outer_gather<<<G, kBBlock, 0, s>>>(B.L);
+          k_batched_outer_residual<<<G, kBBlock, 0, s>>>(B.d_desc, B.L, 0.0, 0.0, 1 << 30, 50);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+          rc = fail(BS_ERR_CUDA, "bs_cg_batched_autotune: start launch");
+          break;
+        }
+        rc = f32 ? launch_iter<float>(B, s) : launch_iter<double>(B, s);
+        if (!rc) BS_CUDA_TRY(cudaEventRecord(e0, s));
+        for (int k = 0; k < iters && !rc; ++k)
+          rc = f32 ? launch_iter<float>(B, s) : launch_iter<double>(B, s);
+        if (rc) break;
+        BS_CUDA_TRY(cudaEventRecord(e1, s));
+        BS_CUDA_TRY(cudaEventSynchronize(e1));
+        if ((rc = read_flags(B, s))) break;
+        if (B.h_flags[0]) {
+          rc = fail(B.h_flags[0], "bs_cg_batched_autotune: device barrier timed out");
+          break;
+        }
+        float ms = 0.f;
+        BS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / iters;
+        if (per < bestv) {
+          bestv = per;
+          *best = cfg;
+        }
+      }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  for (double *p : xs) cudaFree(p);
+  if (!rc && best_ms) *best_ms = bestv;
+  return rc;
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+int bs_cg_solve_batched(int32_t nsolves, const bs_problem *const *probs, const double *const *b,
+                        double *const *x, double tol, int32_t maxit, int32_t flags,
+                        bs_cg_info *infos, void *stream) {
+  return solve_batched(nsolves, probs, b, x, tol, maxit, flags, nullptr, infos, stream);
+}
+
+int bs_cg_solve_batched_ex(int32_t nsolves, const bs_problem *const *probs,
+                           const double *const *b, double *const *x, double tol, int32_t maxit,
+                           int32_t flags, const bs_batched_config *cfg, bs_cg_info *infos,
+                           void *stream) {
+  return solve_batched(nsolves, probs, b, x, tol, maxit, flags, cfg, infos, stream);
+}
+
+int bs_cg_batched_autotune(int32_t nsolves, const bs_problem *const *probs,
+                           const double *const *b, int32_t flags, int32_t iters,
+                           bs_batched_config *best, double *ms_per_iteration, void *stream) {
+  return autotune(nsolves, probs, b, flags, iters, best, ms_per_iteration, stream);
+}
+
+}  // extern "C"

@@ -107,3 +107,75 @@ def test_batched_rejects_bad_batches():
     t = torch.zeros(m.NG, dtype=torch.float64, device="cuda")
     with pytest.raises(bs.BSError):
         bs.solve_batched([P9], [t], [t.clone()])
+
+
+def test_batched_ff_operator_matches_fp64_batch():
+    """BS_CG_FF_OPERATOR in the batched FP64 form: every solve meets the
+    tolerance on the FP64 oracle's true residual, in about the iterations of
+    the FP64 batch."""
+    specs = [(2, 4), (5, 2), (8, 2), (3, 5), (7, 2)]
+    items = make(specs, 300)
+    probs = [it[2] for it in items]
+    bs_ = [torch.from_numpy(it[3]).cuda() for it in items]
+    xs = [torch.zeros_like(b) for b in bs_]
+    rc, infos = bs.solve_batched(probs, bs_, xs, tol=1e-8, flags=bs.BS_CG_FF_OPERATOR)
+    xs64 = [torch.zeros_like(b) for b in bs_]
+    rc64, infos64 = bs.solve_batched(probs, bs_, xs64, tol=1e-8)
+    assert rc == 0 and rc64 == 0
+    for (m, Z, P, bh), x, i, i64 in zip(items, xs, infos, infos64):
+        N = m.N
+        r = bh - oracle.apply_A(m.E, N, m.h, 1.0, m.ids, m.NG, x.cpu().numpy())
+        assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(bh)
+        assert abs(i["iterations"] - i64["iterations"]) <= max(3, 0.02 * i64["iterations"])
+
+
+@pytest.mark.parametrize("cfg", [dict(chunk=2048, blocks_per_sm=1, unroll=2),
+                                 dict(chunk=16384, blocks_per_sm=0, unroll=8),
+                                 dict(chunk=1024, blocks_per_sm=2, unroll=1)])
+def test_batched_config_is_deterministic_and_accurate(cfg):
+    specs = [(2, 4), (4, 3), (6, 2), (1, 7)]
+    items = make(specs, 400)
+    probs = [it[2] for it in items]
+    bs_ = [torch.from_numpy(it[3]).cuda() for it in items]
+    runs = []
+    for _ in range(2):
+        xs = [torch.zeros_like(b) for b in bs_]
+        rc, infos = bs.solve_batched(probs, bs_, xs, tol=1e-9, config=cfg,
+                                     flags=bs.BS_CG_GRAPH)
+        assert rc == 0
+        runs.append((xs, infos))
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert torch.equal(a, b)
+    xs_d = [torch.zeros_like(b) for b in bs_]
+    bs.solve_batched(probs, bs_, xs_d, tol=1e-9)
+    for x, xd in zip(runs[0][0], xs_d):
+        assert torch.linalg.norm(x - xd) <= 1e-6 * torch.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("flags", [0, bs.BS_CG_REFINED_F32, bs.BS_CG_FF_OPERATOR])
+def test_autotune_picks_a_candidate_and_it_solves(flags):
+    specs = [(2, 6), (3, 4), (5, 3), (8, 2)]
+    items = make(specs, 500)
+    probs = [it[2] for it in items]
+    bs_ = [torch.from_numpy(it[3]).cuda() for it in items]
+    best, ms = bs.autotune_batched(probs, bs_, flags=flags, iters=3)
+    assert best.chunk in (2048, 4096, 8192, 16384)
+    assert best.unroll in (2, 4, 8) and best.blocks_per_sm in (0, 1)
+    assert ms > 0.0
+    xs = [torch.zeros_like(b) for b in bs_]
+    rc, infos = bs.solve_batched(probs, bs_, xs, tol=1e-8, flags=flags, config=best)
+    assert rc == 0 and all(i["rel_residual"] <= 1e-8 for i in infos)
+
+
+def test_batched_rejects_bad_config_and_flags():
+    items = make([(2, 3)], 600)
+    probs = [items[0][2]]
+    b = [torch.from_numpy(items[0][3]).cuda()]
+    x = [torch.zeros_like(b[0])]
+    rc, _ = bs.solve_batched(probs, b, x, config=dict(chunk=3000), check=False)
+    assert rc == bs.BS_ERR_ARG
+    rc, _ = bs.solve_batched(probs, b, x, config=dict(unroll=3), check=False)
+    assert rc == bs.BS_ERR_ARG
+    rc, _ = bs.solve_batched(probs, b, x, flags=bs.BS_CG_REFINED_F32 | bs.BS_CG_FF_OPERATOR,
+                             check=False)
+    assert rc == bs.BS_ERR_ARG
