@@ -513,7 +513,7 @@ def traffic_for(kernel, op):
             d = json.load(f)
         ent = d["ops"][op]
         from paper_2009_10917_gb300 import build
-        if ent.get("source_sha") != build.source_digest(build.STREAM_SOURCES):
+        if ent.get("source_sha") != build.source_digest(build.OP_SOURCES[op]):
             return None
         return ent["dram_bytes_per_launch_full"]
     except Exception:
