@@ -32,20 +32,39 @@ constexpr int kPrepBlock = 256;  // 8 warps, one element per warp
 
 // One warp per element: u = D^-1 r through the map, rms, the X row as the
 // GEMM operand ([hi] or [hi | hi | lo], padding zero), and rms * oscale to
-// rmsv[e] (0 for an all-zero element).  GB300's FP64 pipe (and the
+// rmsv[e] in double (0 for an all-zero element).  GB300's FP64 pipe (and the
 // conversions, which share it) runs at 1/64 of the FP32 rate, so no node
-// touches it: u = D^-1 r is formed in FP32 from the 24-bit high parts of the
-// exact float-pair splits of D^-1 and r (relative error below 2^-22, far
-// under the network's 2^-16), and the sum of squares and the scaling are FP32.
-// rms is only a normalisation: the network's output is multiplied back by the
-// same value, so its rounding does not matter.
+// touches it: r and D^-1 are brought to [1, 2) relative to their largest
+// value in the element by an exponent shift and truncated to their 24-bit
+// high parts, all by integer operations (relative error below 2^-23 each);
+// u, the sum of squares and the scaling are FP32, and the shift is added
+// back to rms, in double, once per element.  Values more than 2^-126 below
+// the element's largest count as zero.  rms is only a normalisation: the
+// network's output is multiplied back by the same value.
 constexpr int kPrepMaxNq = 10;  // degrees up to 9
+
+// Biased exponent of a double (0 for zero and subnormals).
+__device__ __forceinline__ int dexp(double x) {
+  return ((unsigned)__double2hiint(x) >> 20) & 0x7ff;
+}
+// x 2^(1023 - emax), truncated to 24 significant bits, as a float; 0 when
+// that is below 2^-126 (or x is zero or subnormal).
+__device__ __forceinline__ float shifted_hi(double x, int emax) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const int E = (int)((hw >> 20) & 0x7ffu);
+  const int fe = E - emax + 127;  // float exponent field of the shifted value
+  if (E == 0 || fe < 1) return 0.f;
+  return __uint_as_float((hw & 0x80000000u) | ((unsigned)fe << 23) | ((hw & 0xfffffu) << 3) |
+                         (lw >> 29));
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kPrepBlock)
     k_fp_prep(int64_t E, int Dp, int split, float oscale, const int32_t *__restrict__ order,
               const int32_t *__restrict__ ids, const double *__restrict__ r,
               const double *__restrict__ dinv, __nv_bfloat16 *__restrict__ X,
-              float *__restrict__ rmsv, const CgState *st) {
+              double *__restrict__ rmsv, const CgState *st) {
   constexpr int T = (NP + 31) / 32;  // nodes per lane
   if (cg_halted(st)) return;
   const int lane = threadIdx.x & 31;
@@ -67,11 +86,22 @@ __global__ void __launch_bounds__(kPrepBlock)
     rv[t] = g[t] >= 0 ? __ldg(r + g[t]) : 0.0;
     dv[t] = g[t] >= 0 ? __ldg(dinv + g[t]) : 0.0;
   }
+  int er = 0, ed = 0;  // largest exponents in the element
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    er = max(er, dexp(rv[t]));
+    ed = max(ed, dexp(dv[t]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    er = max(er, __shfl_xor_sync(0xffffffffu, er, o));
+    ed = max(ed, __shfl_xor_sync(0xffffffffu, ed, o));
+  }
   float uf[T];
   float ss = 0.f;
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    uf[t] = ff_split(dv[t]).hi * ff_split(rv[t]).hi;
+    uf[t] = shifted_hi(dv[t], ed) * shifted_hi(rv[t], er);
     ss = fmaf(uf[t], uf[t], ss);
   }
 #pragma unroll
@@ -91,12 +121,13 @@ __global__ void __launch_bounds__(kPrepBlock)
       row[2 * Dp + l] = lo;
     }
   }
-  if (lane == 0) rmsv[q] = rms * oscale;
+  // the true rms: undo the two shifts (2^(er - 1023) and 2^(ed - 1023))
+  if (lane == 0) rmsv[q] = rms > 0.f ? ldexp((double)(rms * oscale), er + ed - 2046) : 0.0;
 }
 
 static int launch_fp_prep(int N, int64_t E, int Dp, int split, float oscale, const int32_t *order,
                           const int32_t *ids, const double *r, const double *dinv,
-                          __nv_bfloat16 *X, float *rmsv, const CgState *st, cudaStream_t s) {
+                          __nv_bfloat16 *X, double *rmsv, const CgState *st, cudaStream_t s) {
   const unsigned grid = (unsigned)((E + kPrepBlock / 32 - 1) / (kPrepBlock / 32));
 #define BS_PREP_CASE(NQ)                                                                     \
   case NQ:                                                                                   \
@@ -178,34 +209,30 @@ __device__ void fpcg_scalars(CgState *st, double rzn, double rzo, double rzj, in
 // r.z', r.z_old, r.(D^-1 r); z holds the old z on entry and z' on exit.  z'
 // is one FP64 fused multiply-add per node; the dot products run on the FP32
 // pipes as float-pair sums of exact float-pair splits (error a few units of
-// 2^-46 of the sum of |terms|), so the kernel is bound by HBM, not by
-// GB300's narrow FP64 pipe.
+// 2^-46 of the sum of |terms|), falling back to FP64 for values outside
+// [2^-60, 2^60), so the kernel is bound by HBM, not by GB300's narrow FP64
+// pipe, at any scale of the data.
 __global__ void __launch_bounds__(kReduceBlock)
     k_fpcg_z(int64_t NG, const double *__restrict__ r, const double *__restrict__ dinv,
              const double *__restrict__ corr, double *__restrict__ z, double *partials,
              unsigned int *counter, CgState *st, int init, int have_mlp) {
   if (cg_halted(st)) return;
   FF an{0.f, 0.f}, ao{0.f, 0.f}, aj{0.f, 0.f};
+  double dn = 0.0, dlo = 0.0, dj = 0.0;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = tid; g < NG; g += nth) {
     const double rg = r[g], dg = dinv[g];
-    const double zn = have_mlp ? fma(dg, rg, corr[g]) : dg * rg;
-    const FF rs = ff_split(rg), ds = ff_split(dg), zs = ff_split(zn);
-    if (!init) {
-      const FF zo = ff_split(z[g]);
-      ff_fma(ao, rs.hi, rs.lo, zo.hi, zo.lo);
-    }
-    ff_fma(an, rs.hi, rs.lo, zs.hi, zs.lo);
-    // r (D^-1 r): the product D^-1 r as an unevaluated pair, then times r
-    FF j{0.f, 0.f};
-    ff_fma(j, ds.hi, ds.lo, rs.hi, rs.lo);
-    ff_fma(aj, j.hi, j.lo, rs.hi, rs.lo);
+    const double zj = dg * rg;
+    const double zn = have_mlp ? fma(dg, rg, corr[g]) : zj;
+    if (!init) ff_dot_acc(ao, dlo, rg, z[g]);
+    ff_dot_acc(an, dn, rg, zn);
+    ff_dot_acc(aj, dj, rg, zj);
     z[g] = zn;
   }
-  const double pn = block_sum<kReduceBlock>(ff_widen(an.hi) + ff_widen(an.lo));
-  const double po = block_sum<kReduceBlock>(ff_widen(ao.hi) + ff_widen(ao.lo));
-  const double pj = block_sum<kReduceBlock>(ff_widen(aj.hi) + ff_widen(aj.lo));
+  const double pn = block_sum<kReduceBlock>(ff_widen(an.hi) + ff_widen(an.lo) + dn);
+  const double po = block_sum<kReduceBlock>(ff_widen(ao.hi) + ff_widen(ao.lo) + dlo);
+  const double pj = block_sum<kReduceBlock>(ff_widen(aj.hi) + ff_widen(aj.lo) + dj);
   double tn, to, tj;
   if (grid_combine3<kReduceBlock>(pn, po, pj, partials, counter, &tn, &to, &tj) &&
       threadIdx.x == 0)
@@ -303,7 +330,7 @@ static int precondition(const bs_problem *P, bs_mlp *mlp, int odd, int init, cud
   const int Np = (P->N + 1) * (P->N + 1) * (P->N + 1);
   if (mlp) {
     const int64_t E = m->E;
-    float *rmsv = mlp->Y;  // E floats of inference scratch
+    double *rmsv = reinterpret_cast<double *>(mlp->Y);  // E doubles of inference scratch
     if (int rc = launch_fp_prep(P->N, E, mlp->Dp, mlp->split, 1.0f, m->d_elem_order, m->d_ids,
                                 v.r, v.dinv, mlp->Xb, rmsv, st, s))
       return rc;

@@ -139,11 +139,11 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_tn(GemmArgs g) {
                                ? __float2bfloat16_rn(v)
                                : __float2bfloat16_rn(0.f);
           } else if (EPI == EPI_SCALE_F64) {
-            if (n + e < g.nvalid) g.out_f64[o] = (double)v * (double)g.scale[m];
+            if (n + e < g.nvalid) g.out_f64[o] = (double)v * g.scale[m];
           } else {
             if (n + e < g.nvalid) {
               const int32_t gid = idrow[g.lidx[n + e]];
-              if (gid >= 0) g.out_f64[gid] = (double)v * (double)g.scale[m];
+              if (gid >= 0) g.out_f64[gid] = (double)v * g.scale[m];
             }
           }
         }

@@ -78,7 +78,7 @@ struct GemmArgs {
   double *out_f64;
   const __nv_bfloat16 *mask;
   int ldmask, relu, split;
-  const float *scale;
+  const double *scale;  // EPI_SCALE_F64 / EPI_SCATTER_F64: per-row factor
   const int32_t *ids, *order, *lidx;  // EPI_SCATTER_F64: map, row -> element, local indices
   int np;
   const CgState *st;  // optional: skip the launch when a solve has stopped

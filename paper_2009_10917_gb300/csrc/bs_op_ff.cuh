@@ -84,6 +84,22 @@ __device__ __forceinline__ void ff_fma(FF &s, float a, float al, float b, float 
   s.lo = s.lo + (err + c);
 }
 
+// Dot-product step safe at any scale: acc (a float pair) += a b when both
+// lie in [2^-60, 2^60) (products, their rounding errors and the low parts
+// then stay normal floats), else dacc = fma(a, b, dacc) on the FP64 pipe;
+// zeros and subnormals contribute nothing.  The caller adds dacc to the
+// widened pair.
+__device__ __forceinline__ void ff_dot_acc(FF &acc, double &dacc, double a, double b) {
+  const unsigned ea = ((unsigned)__double2hiint(a) >> 20) & 0x7ffu;
+  const unsigned eb = ((unsigned)__double2hiint(b) >> 20) & 0x7ffu;
+  if (ea - 963u < 120u && eb - 963u < 120u) {
+    const FF x = ff_split(a), y = ff_split(b);
+    ff_fma(acc, x.hi, x.lo, y.hi, y.lo);
+  } else if (ea != 0u && eb != 0u) {
+    dacc = fma(a, b, dacc);
+  }
+}
+
 // out = A_L in on elements slot0 .. slot0 + EPB - 1, as ax_elements.
 template <int NQ, bool GATHER_IN>
 __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,

@@ -245,3 +245,22 @@ def test_trained_network_gain():
                                          coef=coef)
     assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(b.cpu().numpy())
     assert il["iterations"] <= 0.8 * ij["iterations"], (il["iterations"], ij["iterations"])
+
+
+def test_fpcg_is_scale_invariant():
+    """The float-pair dot products fall back to FP64 outside [2^-60, 2^60):
+    a right-hand side scaled by 2^-110 (or 2^100) takes the same steps and
+    gives the same solution, scaled."""
+    coef = synth.lognormal(3 ** 3, 2)
+    m, Z, P = _problem(3, 3, 1e-2, coef)
+    W1, W2 = weights(64, 64, 4)
+    net = bs.MLP(W1, (0.05 * W2).astype(np.float32), split=True)
+    b = torch.from_numpy(synth.uniform(m.NG, 3)).cuda()
+    x1, i1 = bs.fpcg_learned(P, net, b, tol=1e-9, flags=bs.BS_FPCG_ODD)
+    for sc in (2.0 ** -110, 2.0 ** 100):
+        xs, is_ = bs.fpcg_learned(P, net, b * sc, tol=1e-9, flags=bs.BS_FPCG_ODD)
+        assert is_["rc"] == 0
+        assert abs(is_["iterations"] - i1["iterations"]) <= 2
+        # the network's input is scale-free (rms normalisation), so only
+        # rounding separates the two solves
+        assert torch.linalg.norm(xs / sc - x1) <= 1e-7 * torch.linalg.norm(x1)
