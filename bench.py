@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "per-op HBM GB/s (% of GB300 peak); time-to-1e-8 CG solve, plain vs batched/learned"
 OPS = ["copy", "axpy", "norm", "dot", "cg_update", "scatter", "gather"]
 KERNEL_OF = {"copy": "k_copy", "axpy": "k_axpy", "norm": "k_dot", "dot": "k_dot",
-             "cg_update": "k_cg_update", "scatter": "k_scatter", "gather": "k_gather"}
+             "cg_update": "k_cg_update", "scatter": "k_scatter2", "gather": "k_gather"}
 
 
 def parse():
