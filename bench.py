@@ -141,6 +141,27 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- multi-rank
+
+def max_over_ranks(ms, world, device="cuda"):
+    """The slowest rank's time: an all-reduce MAX over the job (identity for
+    one rank).  device: where the scalar lives for the backend (cuda for
+    NCCL, cpu for gloo)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_step, steps, world, ms):
+    """Whole-job GB/s: every rank moves bytes_per_step per step (replicas),
+    over the slowest rank's time."""
+    return world * bytes_per_step * steps / (ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- inputs
 
 def make_inputs(args):
@@ -227,13 +248,10 @@ def run_ours(args):
     total_ms = t0e.elapsed_time(t1e)
     per_op_ms = {op: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps
                  for i, op in enumerate(OPS)}
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     B = alg_bytes(n, NL, NG)
     step_bytes = sum(B.values())
-    value = world * step_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_throughput(step_bytes, args.steps, world, total_ms)
     peak, peak_kind = peaks()
     per_op = {op: {"gbs": round(B[op] / (per_op_ms[op] * 1e-3) / 1e9, 1),
                    "ms": round(per_op_ms[op], 4),
@@ -272,12 +290,8 @@ def run_ours(args):
         b_.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = a.elapsed_time(b_)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": round(world * step_bytes * ksteps / (ems * 1e-3) / 1e9, 1), "unit": "GB/s",
+        ems = max_over_ranks(a.elapsed_time(b_), world)
+        e2e = {"value": round(job_throughput(step_bytes, ksteps, world, ems), 1), "unit": "GB/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 32, "steps": ksteps}
 
     cpu = None
