@@ -325,6 +325,17 @@ enum {
   BS_FPCG_NO_JUDGE = 128  /* bs_fpcg_learned: never switch to Jacobi for good */
 };
 
+/* Engine of the network's GEMMs, process-wide: 0 (the default) runs every
+ * GEMM on mma.sync (bf16 -> fp32); 1 runs them on the tcgen05 tensor cores
+ * (accumulator in tensor memory, operands staged by cp.async in the
+ * canonical K-major layout) wherever the shape allows -- K a multiple of 8,
+ * 16-byte aligned operands, any epilogue but the relu' mask of the backward
+ * pass.  Both give bitwise identical results; at the learned
+ * preconditioner's shapes the mma.sync kernel is measured faster (97 vs
+ * 137 us for the interior GEMM at N = 5 on 48^3).  Returns the previous
+ * engine; any other value only queries it. */
+int bs_gemm_engine(int32_t engine);
+
 /* Create a network from HOST weights h_W1 [H x D], h_W2 [D x H] (copied).
  * 1 <= D <= 4096; H a multiple of 32 in [32, 4096].  flags: 0 or
  * BS_MLP_BF16X3.  Synchronous.  Adam state starts at zero. */

@@ -427,6 +427,7 @@ def autotune_batched(problems, bs_, flags=0, iters=4):
 # ---------------------------------------------------------------- learned preconditioner
 
 _SIGS.update({
+    "bs_gemm_engine": (ctypes.c_int, [_i32]),
     "bs_mlp_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _pp]),
     "bs_mlp_destroy": (ctypes.c_int, [_vp]),
     "bs_mlp_get_weights": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -450,6 +451,12 @@ def _bind(names):
 
 def _fptr(t, name="tensor"):
     return _ptr(t, torch.float32, name)
+
+
+def gemm_engine(engine=-1):
+    """bs_gemm_engine: 0 mma.sync (default), 1 tcgen05; returns the previous
+    engine (-1: query only)."""
+    return _bind(["bs_gemm_engine"]).bs_gemm_engine(int(engine))
 
 
 class MLP:

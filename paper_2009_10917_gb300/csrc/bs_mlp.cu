@@ -122,30 +122,7 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_tn(GemmArgs g) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if (n + e >= g.N) continue;
-          const float v = acc[mt][nt][2 * h + e];
-          const int64_t o = m * g.ldc + n + e;
-          if (EPI == EPI_F32) {
-            g.out_f32[o] = v;
-          } else if (EPI == EPI_HIDDEN) {
-            __nv_bfloat16 hi, lo;
-            bf16_split(g.relu ? (v > 0.f ? v : 0.f) : v, hi, lo);
-            g.out_b16[o] = hi;
-            if (g.split) {
-              g.out_b16[o + g.split] = hi;
-              g.out_b16[o + 2 * g.split] = lo;
-            }
-          } else if (EPI == EPI_MASK_BF16) {
-            g.out_b16[o] = __bfloat162float(g.mask[m * g.ldmask + n + e]) > 0.f
-                               ? __float2bfloat16_rn(v)
-                               : __float2bfloat16_rn(0.f);
-          } else if (EPI == EPI_SCALE_F64) {
-            if (n + e < g.nvalid) g.out_f64[o] = (double)v * g.scale[m];
-          } else {
-            if (n + e < g.nvalid) {
-              const int32_t gid = idrow[g.lidx[n + e]];
-              if (gid >= 0) g.out_f64[gid] = (double)v * g.scale[m];
-            }
-          }
+          gemm_store<EPI>(g, m, n + e, acc[mt][nt][2 * h + e], idrow);
         }
       }
     }
@@ -163,6 +140,7 @@ static void launch_epi(const GemmArgs &a, int64_t gy, cudaStream_t s) {
 int launch_gemm(int epi, const GemmArgs &a, cudaStream_t s) {
   if (a.K % GBK) return fail(BS_ERR_ARG, "gemm: K = %d is not a multiple of %d", a.K, GBK);
   if (a.M <= 0 || a.N <= 0) return BS_OK;
+  if (gemm_tc_supported(epi, a)) return launch_gemm_tc(epi, a, a.err, s);
   const int64_t gy = (a.M + GBM - 1) / GBM;
   if (gy > 65535) return fail(BS_ERR_ARG, "gemm: M too large");
   switch (epi) {

@@ -69,6 +69,12 @@ enum GemmEpi {
                       // out_f64[gid] = acc * scale[m]
 };
 
+// hi/lo bf16 split of a float (lo = 0 unless split)
+__device__ __forceinline__ void bf16_split(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 struct GemmArgs {
   const __nv_bfloat16 *A, *B;  // A [M x K], B [N x K], row-major
   int64_t M;
@@ -82,7 +88,41 @@ struct GemmArgs {
   const int32_t *ids, *order, *lidx;  // EPI_SCATTER_F64: map, row -> element, local indices
   int np;
   const CgState *st;  // optional: skip the launch when a solve has stopped
+  int *err;           // optional: set to 2 if a tensor-core wait gives up
 };
+
+// Epilogue of one accumulator value v at (m, n) (idrow: the map row of
+// element order[m], EPI_SCATTER_F64 only).
+template <int EPI>
+__device__ __forceinline__ void gemm_store(const GemmArgs &g, int64_t m, int n, float v,
+                                           const int32_t *idrow) {
+  const int64_t o = m * g.ldc + n;
+  if (EPI == EPI_F32) {
+    g.out_f32[o] = v;
+  } else if (EPI == EPI_HIDDEN) {
+    __nv_bfloat16 hi, lo;
+    bf16_split(g.relu ? (v > 0.f ? v : 0.f) : v, hi, lo);
+    g.out_b16[o] = hi;
+    if (g.split) {
+      g.out_b16[o + g.split] = hi;
+      g.out_b16[o + 2 * g.split] = lo;
+    }
+  } else if (EPI == EPI_MASK_BF16) {
+    g.out_b16[o] = __bfloat162float(g.mask[m * g.ldmask + n]) > 0.f ? __float2bfloat16_rn(v)
+                                                                    : __float2bfloat16_rn(0.f);
+  } else if (EPI == EPI_SCALE_F64) {
+    if (n < g.nvalid) g.out_f64[o] = (double)v * g.scale[m];
+  } else {
+    if (n < g.nvalid) {
+      const int32_t gid = idrow[g.lidx[n]];
+      if (gid >= 0) g.out_f64[gid] = (double)v * g.scale[m];
+    }
+  }
+}
+
+// The tcgen05 path (bs_tc.cu): whether a GEMM can take it, and its launch.
+bool gemm_tc_supported(int epi, const GemmArgs &a);
+int launch_gemm_tc(int epi, const GemmArgs &a, int *err, cudaStream_t s);
 
 int launch_gemm(int epi, const GemmArgs &a, cudaStream_t s);
 // Hidden layer then output layer on the activation operand m->Xb (B rows,
@@ -91,11 +131,7 @@ int launch_gemm(int epi, const GemmArgs &a, cudaStream_t s);
 int mlp_forward_packed(bs_mlp *m, int64_t B, int relu, GemmArgs out, int out_epi,
                        cudaStream_t s);
 
-// hi/lo bf16 split of a float (lo = 0 unless split)
-__device__ __forceinline__ void bf16_split(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
-  hi = __float2bfloat16_rn(v);
-  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
+
 // Training/inference scratch for batches (or element counts) up to B rows.
 int mlp_ensure(bs_mlp *m, int64_t B);
 // L = W2 W1 / 2 and its operand Lb, if the weights changed since last formed.

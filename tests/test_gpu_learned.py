@@ -264,3 +264,37 @@ def test_fpcg_is_scale_invariant():
         # the network's input is scale-free (rms normalisation), so only
         # rounding separates the two solves
         assert torch.linalg.norm(xs / sc - x1) <= 1e-7 * torch.linalg.norm(x1)
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_tcgen05_engine_matches_mma_sync(split):
+    """The tcgen05 GEMMs (bs_gemm_engine(1)) against the mma.sync ones: the
+    forward pass of every epilogue they serve, the loss gradients and a few
+    flexible-PCG iterations agree bitwise (both sum 16-wide K blocks in FP32
+    in the same order); sizes with a partial 64-wide K chunk and M tails."""
+    D, H = 216, 256
+    W1, W2 = weights(D, H, 13)
+    net = bs.MLP(W1, W2, split=split)
+    X = torch.from_numpy(synth.uniform(300 * D, 14).reshape(300, D).astype(np.float32)).cuda()
+    T = torch.from_numpy(synth.uniform(256 * D, 15).reshape(256, D).astype(np.float32)).cuda()
+    coef = synth.lognormal(3 ** 3, 2)
+    m, Z, P = _problem(3, 5, 1e-2, coef)
+    b = torch.from_numpy(synth.uniform(m.NG, 16)).cuda()
+    out = {}
+    prev = bs.gemm_engine(-1)
+    try:
+        for eng in (0, 1):
+            bs.gemm_engine(eng)
+            y = net.forward(X)
+            yo = net.forward(X, odd=True)
+            loss, g1, g2 = net.loss_grad(X[:256].contiguous(), T)
+            x, info = bs.fpcg_learned(P, net, b, maxit=12, flags=bs.BS_FPCG_ODD, check=False)
+            x2, info2 = bs.fpcg_learned(P, net, b, maxit=12, check=False)
+            out[eng] = (y, yo, loss, g1, g2, x, info["rr"], x2, info2["rr"])
+    finally:
+        bs.gemm_engine(prev)
+    for a, c in zip(out[0], out[1]):
+        if torch.is_tensor(a):
+            assert torch.equal(a, c)
+        else:
+            assert a == c
