@@ -207,7 +207,10 @@ typedef struct {
  * 3*(maxit+1) doubles: alpha_j at [3j], beta_j at [3j+1], r_{j+1}.r_{j+1} at
  * [3j+2].  flags: BS_CG_FIXED_ITERS, BS_CG_JACOBI, BS_CG_GRAPH, BS_CG_X0,
  * BS_CG_FF_OPERATOR (every A p with the float-float element operator of
- * bs_apply_A_ff; vectors, reductions and updates stay FP64).  Synchronises
+ * bs_apply_A_ff; vectors, reductions and updates stay FP64; the solve runs
+ * on the system scaled by the power of two that brings the RMS of b near 1,
+ * exactly undone on x, so the operator's 2^-102 floor is relative to b;
+ * d_hist then holds the scaled r.r).  Synchronises
  * `stream` before returning; info (host) may be NULL.  Returns
  * BS_ERR_NOT_CONVERGED if maxit is reached without BS_CG_FIXED_ITERS,
  * BS_ERR_BREAKDOWN on p.Ap <= 0. */

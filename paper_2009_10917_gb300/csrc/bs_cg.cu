@@ -126,6 +126,13 @@ __global__ void __launch_bounds__(kReduceBlock)
   }
 }
 
+// v[i] = s * v[i] (s a power of two: exact).
+__global__ void k_scale(int64_t n, double s, double *__restrict__ v) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < n; i += nth) v[i] = s * v[i];
+}
+
 __global__ void k_reciprocal(int64_t n, const double *__restrict__ d, double *__restrict__ inv) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -241,6 +248,7 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
   const bool fixed = flags & BS_CG_FIXED_ITERS;
   const bool precond = flags & BS_CG_JACOBI;
   const bool ff = flags & BS_CG_FF_OPERATOR;
+  double ff_scale = 1.0;  // power of two the FF solve runs scaled by
   CgVecs v = vecs(P);
   CgState *st = P->d_state;
   int rc = BS_OK;
@@ -252,6 +260,26 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
   } while (0)
   {
     if (!(flags & BS_CG_X0)) BS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * NG, s));
+    if (ff && NG > 0) {
+      // The float-float operator counts inputs below 2^-102 as zero: solve
+      // the system scaled by the power of two that brings b's RMS near 1
+      // (exact both ways), with the scaled b in the spare vector.
+      BS_TRY((launch_dot<double, true, EpBB>(NG, b, b, P->d_partials, P->d_counter, EpBB{st},
+                                             nullptr, s)));
+      BS_CUDA_TRY(cudaMemcpyAsync(P->h_state, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+      BS_CUDA_TRY(cudaStreamSynchronize(s));
+      const double bb0 = P->h_state->bb;
+      if (bb0 > 0.0 && std::isfinite(bb0)) {
+        ff_scale = std::ldexp(1.0, -std::ilogb(std::sqrt(bb0 / (double)NG)));
+        double *bs_ = P->d_vec + 5 * (NG + 2);
+        BS_TRY(launch_copy<double>(NG, b, bs_, s));
+        const int grid = stream_grid(NG, 1, kStreamBlock, 8);
+        k_scale<<<grid, kStreamBlock, 0, s>>>(NG, ff_scale, bs_);
+        if (flags & BS_CG_X0) k_scale<<<grid, kStreamBlock, 0, s>>>(NG, ff_scale, x);
+        BS_CUDA_TRY(cudaGetLastError());
+        b = bs_;
+      }
+    }
     BS_TRY((launch_dot<double, true, EpBB>(NG, b, b, P->d_partials, P->d_counter, EpBB{st},
                                            nullptr, s)));
     // r_0 = b - A x_0
@@ -301,9 +329,14 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
                 h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0);
     if (info) {
       info->iterations = h.iter;
-      info->rr = h.rr;
-      info->bb = h.bb;
+      info->rr = h.rr / (ff_scale * ff_scale);
+      info->bb = h.bb / (ff_scale * ff_scale);
       info->rel_residual = h.bb > 0 ? std::sqrt(h.rr / h.bb) : std::sqrt(h.rr);
+    }
+    if (ff_scale != 1.0) {  // back to the unscaled solution (exact)
+      k_scale<<<stream_grid(NG, 1, kStreamBlock, 8), kStreamBlock, 0, s>>>(NG, 1.0 / ff_scale, x);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        rc = fail(BS_ERR_CUDA, "bs_cg_solve: unscaling the solution failed");
     }
   }
 done:

@@ -78,3 +78,27 @@ def test_cg_with_ff_operator(jacobi):
     r = bh - oracle.apply_A(m.E, N, m.h, lam, m.ids, m.NG, x.cpu().numpy(), coef)
     assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(bh)
     assert torch.linalg.norm(x - x64) <= 1e-6 * torch.linalg.norm(x64)
+
+
+def test_ff_cg_is_scale_invariant():
+    """CG with the float-float operator runs the system scaled by the power
+    of two that brings b's RMS near 1 and unscales x (exact), so a right-hand
+    side of 2^-110 or 2^100 takes the same steps; the hist-free info reports
+    the unscaled r.r and b.b."""
+    N, K, lam = 3, 4, 1e-2
+    m = synth.Mesh(K, N, seed=2)
+    Z = bs.Map(m.E, N, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, lam)
+    b = cuda(synth.uniform(m.NG, 11))
+    x1, i1 = P.cg(b, tol=1e-9, maxit=5000, flags=bs.BS_CG_FF_OPERATOR)
+    for sc in (2.0 ** -110, 2.0 ** 100):
+        xs, is_ = P.cg(b * sc, tol=1e-9, maxit=5000, flags=bs.BS_CG_FF_OPERATOR)
+        assert is_["rc"] == 0 and is_["iterations"] == i1["iterations"]
+        assert torch.equal(xs / sc, x1)
+        assert is_["bb"] == pytest.approx(i1["bb"] * sc * sc, rel=1e-12)
+    # an initial guess is scaled with b
+    x0 = x1.clone() * 0.5
+    xg, ig = P.cg(b * 2.0 ** -110, x=x0 * 2.0 ** -110, tol=1e-9, maxit=5000,
+                  flags=bs.BS_CG_FF_OPERATOR | bs.BS_CG_X0)
+    assert ig["rc"] == 0
+    assert torch.linalg.norm(xg / 2.0 ** -110 - x1) <= 1e-7 * torch.linalg.norm(x1)
