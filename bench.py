@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--learned-mesh", default="5,64", help="N,K of the learned workload")
     ap.add_argument("--no-plain", action="store_true",
                     help="learned workload: skip the (long) unpreconditioned CG solve")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="default run: skip the compact learned-preconditioner section")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default run: skip the compact batched section")
     ap.add_argument("--nsolves", type=int, default=256, help="solves in the batched workload")
     ap.add_argument("--cg-mesh", default="7,48", help="N,K of the CG time-to-tolerance mesh")
     ap.add_argument("--no-cg-small", action="store_true", help="skip the N=3, 8^3 CG runs")
@@ -297,11 +301,19 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args)
-    cg = None
-    if not args.no_cg:
+    cg = learned = batched = None
+    if not (args.no_cg and args.no_learned and args.no_batched):
         del dev, y, qL, qG2
         torch.cuda.empty_cache()
+    if not args.no_cg:
         cg = cg_section(args)
+        torch.cuda.empty_cache()
+    if not args.no_learned and rank == 0:
+        learned = learned_section(args, compact=True)
+        torch.cuda.empty_cache()
+    if not args.no_batched and rank == 0:
+        batched = batched_section(args, compact=True)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
@@ -310,7 +322,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config(args, n, mesh.N, mesh.K, NL, NG),
                 "per_op": per_op, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 7 * args.steps, "clocks": clk.summary(), "cg": cg}
+                "gpu_launches": 7 * args.steps, "clocks": clk.summary(), "cg": cg,
+                "learned": learned, "batched": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -365,7 +378,7 @@ def cg_section(args):
     return out
 
 
-def batched_section(args):
+def batched_section(args, compact=False):
     """The batched configuration: nsolves independent solves, degree N uniform
     in {2..8}, K uniform in {4..24} (seed 7), lambda = 1, b uniform[-1, 1),
     tol 1e-8.  Runs the autotuner for each form (FP64, FP64 with the
@@ -400,15 +413,19 @@ def batched_section(args):
 
     FF, F32 = bs.BS_CG_FF_OPERATOR, bs.BS_CG_REFINED_F32
     tuned = {}
-    for name, fl in (("fp64", 0), ("fp64_ff_operator", FF), ("fp32_ir", F32)):
+    forms = (("fp64_ff_operator", FF), ("fp32_ir", F32)) if compact else (
+        ("fp64", 0), ("fp64_ff_operator", FF), ("fp32_ir", F32))
+    for name, fl in forms:
         t0 = time.perf_counter()
         cfg, ms = bs.autotune_batched(probs, bs_, flags=fl, iters=4)
         tuned[name] = cfg
         out[f"autotune_{name}"] = {"config": cfg.as_dict(), "ms_per_iteration": round(ms, 3),
                                    "tuning_seconds": round(time.perf_counter() - t0, 2)}
-    runs = [("batched_fp64", 0, None), ("batched_fp64_tuned", 0, tuned["fp64"]),
-            ("batched_fp64_ff_operator_tuned", FF, tuned["fp64_ff_operator"]),
-            ("batched_fp32_ir", F32, None), ("batched_fp32_ir_tuned", F32, tuned["fp32_ir"])]
+    runs = [("batched_fp64_ff_operator_tuned", FF, tuned["fp64_ff_operator"]),
+            ("batched_fp32_ir_tuned", F32, tuned["fp32_ir"])]
+    if not compact:
+        runs = [("batched_fp64", 0, None), ("batched_fp64_tuned", 0, tuned["fp64"])] + runs + [
+            ("batched_fp32_ir", F32, None)]
     for name, fl, cfg in runs:
         dt, (rc, infos) = timed(lambda it: bs.solve_batched(
             probs, bs_, xs, tol=1e-8, maxit=it, flags=bs.BS_CG_GRAPH | fl, check=False,
@@ -429,9 +446,10 @@ def batched_section(args):
             worst = max(worst, info["rel_residual"])
         return worst
 
-    for name, refined, ff in (("sequential_fp64", False, False),
-                              ("sequential_fp64_ff_operator", False, True),
-                              ("sequential_fp32_ir", True, False)):
+    seq = (("sequential_fp64", False, False),) if compact else (
+        ("sequential_fp64", False, False), ("sequential_fp64_ff_operator", False, True),
+        ("sequential_fp32_ir", True, False))
+    for name, refined, ff in seq:
         dt, worst = timed(lambda it: one_by_one(refined, ff, it))
         out[name] = {"seconds": round(dt, 3), "max_rel_residual": worst}
     best = min(("batched_fp64_ff_operator_tuned", "batched_fp32_ir_tuned"),
@@ -442,7 +460,7 @@ def batched_section(args):
     return out
 
 
-def learned_section(args):
+def learned_section(args, compact=False):
     """The learned-preconditioner configuration: degree N=5 on a 64^3 mesh
     (E = 262144, N_G = 321^3), lambda = 1e-2, per-element coefficient
     lognormal(sigma = 1), b uniform[-1, 1), tol 1e-8.  Times plain FP64 CG,
@@ -481,7 +499,7 @@ def learned_section(args):
 
     out = {"mesh": f"N={N} {K}^3", "E": m.E, "N_G": m.NG, "lambda": lam,
            "coef": "lognormal(sigma=1) per element", "tol": 1e-8}
-    if not args.no_plain:
+    if not args.no_plain and not compact:
         out["plain_fp64_cg"] = timed(lambda it: P.cg(b, tol=1e-8, maxit=it,
                                                      flags=bs.BS_CG_GRAPH, check=False))
     out["jacobi_pcg"] = timed(lambda it: P.cg(b, tol=1e-8, maxit=it,
@@ -496,9 +514,9 @@ def learned_section(args):
     out["learned_fpcg_odd"] = res
     out["learned_fpcg_odd_ff_operator"] = timed(lambda it: bs.fpcg_learned(
         P, net, b, tol=1e-8, maxit=it, flags=bs.BS_CG_GRAPH | bs.BS_FPCG_ODD | FF, check=False))
-    full = timed(lambda it: bs.fpcg_learned(P, net, b, tol=1e-8, maxit=it,
-                                            flags=bs.BS_CG_GRAPH, check=False))
-    out["learned_fpcg_full_network"] = full
+    if not compact:
+        out["learned_fpcg_full_network"] = timed(lambda it: bs.fpcg_learned(
+            P, net, b, tol=1e-8, maxit=it, flags=bs.BS_CG_GRAPH, check=False))
     for k in [k for k in ("plain_fp64_cg", "jacobi_pcg") if k in out]:
         out[f"speedup_learned_vs_{k}"] = round(out[k]["seconds"] / res["seconds"], 3)
         out[f"iteration_ratio_{k}_over_learned"] = round(
