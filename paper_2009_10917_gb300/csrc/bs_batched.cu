@@ -47,7 +47,6 @@ struct BDesc {
   const OpTab<double> *tab;
   const OpTab<float> *tabf;
   const OpTabFF *tabff;
-  int ff;  // FP64 form: the float-float element operator
   double g, mlam;
   double *x, *r, *p, *Ap, *ApL;  // FP64 (x: the solution)
   const double *b;
@@ -613,7 +612,7 @@ static int read_flags(Batch &B, cudaStream_t s) {
 }
 
 static int build_batch(Batch &B, int ns, const bs_problem *const *P, const double *const *b,
-                       double *const *x, bool f32, bool ff) {
+                       double *const *x, bool f32) {
   B.ns = ns;
   std::vector<BDesc> desc((size_t)ns);
   B.hA.assign((size_t)ns, {});
@@ -637,7 +636,6 @@ static int build_batch(Batch &B, int ns, const bs_problem *const *P, const doubl
     d.tab = p->d_tab;
     d.tabf = p->d_tabf;
     d.tabff = p->d_tabff;
-    d.ff = ff ? 1 : 0;
     d.g = 0.5 * p->h;
     d.mlam = p->lambda * d.g * d.g * d.g;
     const int64_t sv = m->NG + 2;
@@ -841,7 +839,7 @@ static int setup_batch(Batch &B, int32_t nsolves, const bs_problem *const *probs
   if (cfg && cfg->chunk) B.chunk = cfg->chunk;
   if (cfg && cfg->unroll) B.unroll = cfg->unroll;
   B.ff = flags & BS_CG_FF_OPERATOR;
-  if (int rc = build_batch(B, nsolves, probs, b, x, f32, B.ff)) return rc;
+  if (int rc = build_batch(B, nsolves, probs, b, x, f32)) return rc;
   B.grid_iter = occupancy_grid(f32 ? iter_kernel<float>(B.unroll)
                                    : iter_kernel<double>(B.unroll, B.ff),
                                cfg ? cfg->blocks_per_sm : 0);

@@ -12,7 +12,10 @@ accumulation order (1e-5).  Training pairs: the element-interior error from
 the GPU's per-element CG against the oracle's dense Cholesky solve.
 Flexible PCG: with no network, or a network whose output is zero, it is
 Jacobi-PCG; with a linear correction it follows the oracle; a network trained
-on the GPU needs fewer iterations than Jacobi-PCG (test_trained_network_gain).
+on the GPU needs fewer iterations than Jacobi-PCG (test_trained_network_gain);
+the Jacobi judge catches a network that stalls the solve; the solve is
+invariant under power-of-two scaling of b.  The tcgen05 GEMM engine gives
+bitwise the results of the mma.sync one.
 """
 import numpy as np
 import pytest
