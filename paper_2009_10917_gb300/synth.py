@@ -90,10 +90,16 @@ def permutation(n: int, seed: int, stream: int = 99) -> np.ndarray:
 class Mesh:
     """Structured K^3 hex mesh of the unit cube, degree N, permuted elements.
 
-    Attributes: K, N, Nq, Np, E, NL, NG, h, ids (int32[NL]), perm (int64[E]).
+    Attributes: K, N, Nq, Np, E, NL, NG, h, ids (int32[NL]), perm (int64[E]),
+    grid (int64[NG]: the lexicographic grid index (gx + G (gy + G gz)) of each
+    global node).  dirichlet=True masks every local copy of a node on the
+    cube's boundary (id -1) and numbers the (G-2)^3 interior nodes
+    lexicographically, so that A is the operator with homogeneous Dirichlet
+    conditions.
     """
 
-    def __init__(self, K: int, N: int, seed: int | None = 1, permute: bool = True):
+    def __init__(self, K: int, N: int, seed: int | None = 1, permute: bool = True,
+                 dirichlet: bool = False):
         self.K, self.N = int(K), int(N)
         self.Nq = self.N + 1
         self.Np = self.Nq ** 3
@@ -109,6 +115,19 @@ class Mesh:
         else:
             self.perm = np.arange(self.E, dtype=np.int64)
         self.ids = self._build_ids()
+        self.dirichlet = bool(dirichlet)
+        if self.dirichlet:
+            G = self.G
+            g = np.arange(self.NG, dtype=np.int64)
+            gx, gy, gz = g % G, (g // G) % G, g // (G * G)
+            inner = (gx > 0) & (gx < G - 1) & (gy > 0) & (gy < G - 1) & (gz > 0) & (gz < G - 1)
+            new = np.full(self.NG, -1, dtype=np.int64)
+            new[inner] = np.arange(int(inner.sum()), dtype=np.int64)
+            self.grid = g[inner]
+            self.ids = new[self.ids].astype(np.int32)
+            self.NG = int(inner.sum())
+        else:
+            self.grid = np.arange(self.NG, dtype=np.int64)
 
     def element_coords(self, e):
         """(ex, ey, ez) of natural element index e."""

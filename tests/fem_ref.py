@@ -63,7 +63,7 @@ def global_coords(mesh):
     """(x, y, z) of every global node of a structured mesh."""
     r, _, _ = gll_np(mesh.N)
     G, N, h = mesh.G, mesh.N, mesh.h
-    g = np.arange(mesh.NG)
+    g = mesh.grid  # grid index of each global node (Dirichlet meshes skip the boundary)
     gx, gy, gz = g % G, (g // G) % G, g // (G * G)
 
     def coord(t):
