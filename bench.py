@@ -329,6 +329,37 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def operator_times(P, p, reps=20):
+    """Device time of one A p (ms, CUDA events over reps calls after three
+    warm-up calls): FP64 and float-float element kernels, each fused (single-
+    copy nodes written by the element kernel, gather of the shared rows) and
+    unfused (element kernel, gather of every row)."""
+    import torch
+
+    from paper_2009_10917_gb300 import bs
+    out = {}
+    Ap = torch.empty_like(p)
+    prev = bs.operator_fusion(-1)
+    try:
+        for fused in (1, 0):
+            bs.operator_fusion(fused)
+            for name, fn in (("fp64", P.apply_A), ("ff", P.apply_A_ff)):
+                for _ in range(3):
+                    fn(p, Ap)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    fn(p, Ap)
+                e1.record()
+                torch.cuda.synchronize()
+                out[f"{name}_{'fused' if fused else 'unfused'}"] = round(
+                    e0.elapsed_time(e1) / reps, 4)
+    finally:
+        bs.operator_fusion(prev)
+    return out
+
+
 def cg_section(args):
     """Time to tolerance of Algorithm 1 on the GLL Helmholtz operator
     (lambda = 1, b uniform[-1, 1)): plain FP64 CG to 1e-8, the same with the
@@ -369,6 +400,21 @@ def cg_section(args):
                          "outer": info["outer"], "rel_residual": info["rel_residual"],
                          "rel_residual_true_fp64": torch.linalg.norm(r).item() / bn}
             del x, r
+        if not label.startswith("small"):
+            # the same FF solve with the fused operator (single-copy nodes written
+            # by the element kernel, gather of the shared rows)
+            prev = bs.operator_fusion(1)
+            try:
+                runs[1][1]()
+                x, info = runs[1][1]()
+            finally:
+                bs.operator_fusion(prev)
+            res["fp64_cg_ff_operator_fused"] = {"seconds": round(info["seconds"], 4),
+                                                "iterations": info["iterations"]}
+            res["speedup_fused_vs_unfused_ff_cg"] = round(
+                res["fp64_cg_ff_operator"]["seconds"] / info["seconds"], 3)
+            res["operator_ms"] = operator_times(P, b)
+            del x
         for k in ("fp64_cg_ff_operator", "fp32_ir_1e-8"):
             res[f"speedup_{k}_vs_fp64_at_1e-8"] = round(
                 res["fp64_cg"]["seconds"] / res[k]["seconds"], 3)

@@ -101,7 +101,14 @@ _SIGS = {
                                                ctypes.POINTER(CgInfo), _vp]),
     "bs_cg_solve_batched": (ctypes.c_int, [_i32, _vp, _vp, _vp, _d, _i32, _i32,
                                            ctypes.POINTER(CgInfo), _vp]),
+    "bs_operator_fusion": (ctypes.c_int, [_i32]),
 }
+
+
+def operator_fusion(mode=-1):
+    """bs_operator_fusion: 1 fused A p, 0 element kernel + full gather (the
+    default); returns the previous mode (-1: query only)."""
+    return lib().bs_operator_fusion(int(mode))
 
 
 def library_path() -> str:

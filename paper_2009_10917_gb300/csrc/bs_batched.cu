@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(kBBlock, FF ? 3 : (sizeof(T) == 8 ? 2 : 4))
     if (solve_off(d)) continue;
     Acc<T> acc;
     __syncthreads();
-    gather_tile<T, true>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts, d.col_ids, BV<T>::ApL(d),
-                         BV<T>::Ap(d), BV<T>::p(d), smem, acc);
+    gather_tile<T, true, false>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts, d.col_ids, nullptr,
+                                BV<T>::ApL(d), BV<T>::Ap(d), BV<T>::p(d), smem, acc);
     const double part = block_sum<kBBlock>(acc.value());
     double pAp;
     const int4 rg = L.rng[w.x];
@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(kBBlock) k_batched_outer_gather(BLists L) {
     if (d.outer_done) continue;
     Acc<double> acc;
     __syncthreads();
-    gather_tile<double, false>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts, d.col_ids, d.ApL,
-                               d.Ap, nullptr, smem, acc);
+    gather_tile<double, false, false>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts, d.col_ids,
+                                      nullptr, d.ApL, d.Ap, nullptr, smem, acc);
   }
 }
 

@@ -168,19 +168,15 @@ static int pcg_update_launch(const bs_problem *P, double *x, int init, cudaStrea
   return BS_OK;
 }
 
-// One CG iteration (four launches).  ff: the float-float element operator.
+// One CG iteration (four launches: the operator with p.Ap, the fused update
+// with r.r, the direction).  ff: the float-float element operator.
 static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, cudaStream_t s) {
   const bs_map *m = P->map;
   CgVecs v = vecs(P);
   CgState *st = P->d_state;
   const double g = 0.5 * P->h, mlam = P->lambda * g * g * g;
-  int rc = ff ? launch_ax_local_ff<true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, P->d_ApL,
-                                         P->d_tabff, P->d_coef, g, mlam, st, s)
-              : launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p,
-                                              P->d_ApL, P->d_tab, P->d_coef, g, mlam, st, s);
-  if (rc) return rc;
-  rc = launch_gather<double, true, EpAlpha>(m, P->d_ApL, v.Ap, v.p, P->d_partials, P->d_counter,
-                                            EpAlpha{st, precond ? 1 : 0}, st, s);
+  int rc = apply_A_global<double, true, EpAlpha>(P, ff, P->d_tab, v.p, v.Ap, P->d_ApL, g, mlam,
+                                                 EpAlpha{st, precond ? 1 : 0}, st, s);
   if (rc) return rc;
   if (precond) {
     rc = pcg_update_launch(P, x, 0, s);
@@ -194,7 +190,8 @@ static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, c
 }
 
 static int capture_chunk(bs_problem *P, double *x, bool precond, bool ff, int chunk) {
-  const void *key[4] = {x, (const void *)(intptr_t)((precond ? 1 : 0) | (ff ? 2 : 0)),
+  const void *key[4] = {x, (const void *)(intptr_t)((precond ? 1 : 0) | (ff ? 2 : 0) |
+                                                     (g_op_fusion ? 4 : 0)),
                         (const void *)(intptr_t)chunk,
                         (const void *)P->map};
   if (P->graph && key[0] == P->graph_key[0] && key[1] == P->graph_key[1] &&

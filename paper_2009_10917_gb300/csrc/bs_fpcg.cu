@@ -396,13 +396,8 @@ static int fpcg_iteration(const bs_problem *P, bs_mlp *mlp, int odd, bool ff, do
   FpVecs v = fpvecs(P);
   CgState *st = P->d_state;
   const double g = 0.5 * P->h, mlam = P->lambda * g * g * g;
-  int rc = ff ? launch_ax_local_ff<true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, P->d_ApL,
-                                         P->d_tabff, P->d_coef, g, mlam, st, s)
-              : launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p,
-                                              P->d_ApL, P->d_tab, P->d_coef, g, mlam, st, s);
-  if (!rc)
-    rc = launch_gather<double, true, EpAlphaRz>(m, P->d_ApL, v.Ap, v.p, P->d_partials,
-                                                P->d_counter, EpAlphaRz{st}, st, s);
+  int rc = apply_A_global<double, true, EpAlphaRz>(P, ff, P->d_tab, v.p, v.Ap, P->d_ApL, g,
+                                                   mlam, EpAlphaRz{st}, st, s);
   if (!rc)
     rc = launch_cg_update<double, EpResidual>(m->NG, Scalar<double>{0.0, &st->alpha}, v.p, v.Ap,
                                               x, v.r, P->d_partials, P->d_counter,

@@ -50,14 +50,17 @@ struct EpNone {
   __device__ __forceinline__ void operator()(double) const {}
 };
 
-// One tile [lo, hi) of rows: qG[g] = sum over k in [rowStarts[g],
-// rowStarts[g+1]) of qL[colIds[k]], serially from +0 in ascending k; DOT
-// adds w[g] * qG[g] into acc.  A block of kGatherBlock threads calls it
-// together (block barriers inside); s_v holds kTileNnz values.
-template <typename T, bool DOT>
+// One tile [lo, hi) of rows: qG[g] = sum over k in [rowStarts[r],
+// rowStarts[r+1]) of qL[colIds[k]], serially from +0 in ascending k, with
+// g = rows[r] when a row list is given (the shared rows of the fused
+// operator), else g = r; DOT adds w[g] * qG[g] into acc.  A block of
+// kGatherBlock threads calls it together (block barriers inside); s_v holds
+// kTileNnz values.
+template <typename T, bool DOT, bool ROWMAP>
 __device__ __forceinline__ void gather_tile(int2 lo, int2 hi,
                                             const int32_t *__restrict__ row_starts,
                                             const int32_t *__restrict__ col_ids,
+                                            const int32_t *__restrict__ rows,
                                             const T *__restrict__ qL, T *__restrict__ qG,
                                             const T *__restrict__ w, T *s_v, Acc<T> &acc) {
   constexpr int U = kTileNnz / kGatherBlock;  // values per thread per tile
@@ -81,8 +84,9 @@ __device__ __forceinline__ void gather_tile(int2 lo, int2 hi,
       __syncthreads();
       for (int32_t r = r0 + threadIdx.x; r < r1; r += kGatherBlock) {
         const T s = row_sum(s_v, row_starts[r] - k0, row_starts[r + 1] - k0);
-        __stcs(qG + r, s);
-        if (DOT) acc.add(__ldcs(w + r), s);
+        const int32_t g = ROWMAP ? __ldcs(rows + r) : r;
+        __stcs(qG + g, s);
+        if (DOT) acc.add(__ldcs(w + g), s);
       }
       __syncthreads();
     } else {  // a single row longer than a tile: read straight from memory
@@ -91,45 +95,76 @@ __device__ __forceinline__ void gather_tile(int2 lo, int2 hi,
         T s = T(0);
         if (a < b) s = plus_zero(qL[col_ids[a]]);
         for (int32_t k = a + 1; k < b; ++k) s = s + qL[col_ids[k]];
-        qG[r] = s;
-        if (DOT) acc.add(w[r], s);
+        const int32_t g = ROWMAP ? rows[r] : r;
+        qG[g] = s;
+        if (DOT) acc.add(w[g], s);
       }
     }
   }
 }
 
 // The whole gather, tiles in grid-stride order.  DOT: also reduce
-// sum_g w[g] * qG[g] into ep().
-template <typename T, bool DOT, class Ep>
+// sum_g w[g] * qG[g], plus the nextra per-block partials in extra (the fused
+// operator's own terms, summed after the gather's in index order), into ep().
+template <typename T, bool DOT, bool ROWMAP, class Ep>
 __global__ void __launch_bounds__(kGatherBlock)
     k_gather(int64_t ntiles, const int2 *__restrict__ tiles,
              const int32_t *__restrict__ row_starts, const int32_t *__restrict__ col_ids,
-             const T *__restrict__ qL, T *__restrict__ qG, const T *__restrict__ w,
-             double *partials, unsigned int *counter, Ep ep, const CgState *st) {
+             const int32_t *__restrict__ rows, const T *__restrict__ qL, T *__restrict__ qG,
+             const T *__restrict__ w, double *partials, unsigned int *counter,
+             const double *__restrict__ extra, int64_t nextra, Ep ep, const CgState *st) {
   __shared__ T s_v[kTileNnz];
   if (cg_halted(st)) return;
   Acc<T> acc;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-    gather_tile<T, DOT>(tiles[t], tiles[t + 1], row_starts, col_ids, qL, qG, w, s_v, acc);
+    gather_tile<T, DOT, ROWMAP>(tiles[t], tiles[t + 1], row_starts, col_ids, rows, qL, qG, w,
+                                s_v, acc);
   if (DOT) {
     const double part = block_sum<kGatherBlock>(acc.value());
     double total;
-    if (grid_combine<kGatherBlock>(part, partials, counter, &total) && threadIdx.x == 0)
-      ep(total);
+    if (grid_combine<kGatherBlock>(part, partials, counter, &total)) {
+      if (nextra == 0) {
+        if (threadIdx.x == 0) ep(total);
+      } else {
+        double v = 0.0;
+        for (int64_t b = threadIdx.x; b < nextra; b += kGatherBlock) v = v + __ldcg(extra + b);
+        v = block_sum<kGatherBlock>(v);
+        if (threadIdx.x == 0) ep(total + v);
+      }
+    }
   }
+}
+
+// The gather of every row (rows == false) or of the fused operator's shared
+// rows (rows == true), with the optional fused reduction.
+template <typename T, bool DOT, class Ep>
+int launch_gather_rows(const bs_map *m, bool shared, const T *qL, T *qG, const T *w,
+                       double *partials, unsigned int *counter, const double *extra,
+                       int64_t nextra, Ep ep, const CgState *st, cudaStream_t s) {
+  const int64_t nt = shared ? m->nsh_tiles : m->ntiles;
+  auto launch = [&](auto kern) -> int {
+    int grid = stream_grid(nt, 1, 1, blocks_per_sm(kern, kGatherBlock));
+    if (grid < 1) return fail(BS_ERR_CUDA, "no device");
+    if (DOT && grid > kMaxPartials) grid = kMaxPartials;
+    if (shared)
+      kern<<<grid, kGatherBlock, 0, s>>>(nt, m->d_sh_tiles, m->d_sh_starts, m->d_sh_cols,
+                                         m->d_sh_rows, qL, qG, w, partials, counter, extra,
+                                         nextra, ep, st);
+    else
+      kern<<<grid, kGatherBlock, 0, s>>>(nt, m->d_tiles, m->d_row_starts, m->d_col_ids,
+                                         nullptr, qL, qG, w, partials, counter, extra, nextra,
+                                         ep, st);
+    BS_LAUNCH_CHECK();
+    return BS_OK;
+  };
+  return shared ? launch(k_gather<T, DOT, true, Ep>) : launch(k_gather<T, DOT, false, Ep>);
 }
 
 template <typename T, bool DOT, class Ep>
 int launch_gather(const bs_map *m, const T *qL, T *qG, const T *w, double *partials,
                   unsigned int *counter, Ep ep, const CgState *st, cudaStream_t s) {
-  auto kern = k_gather<T, DOT, Ep>;
-  int grid = stream_grid(m->ntiles, 1, 1, blocks_per_sm(kern, kGatherBlock));
-  if (grid < 1) return fail(BS_ERR_CUDA, "no device");
-  if (DOT && grid > kMaxPartials) grid = kMaxPartials;
-  kern<<<grid, kGatherBlock, 0, s>>>(m->ntiles, m->d_tiles, m->d_row_starts, m->d_col_ids, qL,
-                                     qG, w, partials, counter, ep, st);
-  BS_LAUNCH_CHECK();
-  return BS_OK;
+  return launch_gather_rows<T, DOT, Ep>(m, false, qL, qG, w, partials, counter, nullptr, 0, ep,
+                                        st, s);
 }
 
 }  // namespace bs

@@ -33,6 +33,11 @@ static void free_map(bs_map *m) {
   cudaFree(m->d_col_ids);
   cudaFree(m->d_tiles);
   cudaFree(m->d_elem_order);
+  cudaFree(m->d_ids_f);
+  cudaFree(m->d_sh_rows);
+  cudaFree(m->d_sh_starts);
+  cudaFree(m->d_sh_cols);
+  cudaFree(m->d_sh_tiles);
   free(m);
 }
 
@@ -51,6 +56,33 @@ static int do_gather(const bs_map *m, const T *qL, T *qG, void *stream, const ch
   BS_ARG(qG != nullptr && (qL != nullptr || m->NL == 0), "%s: NULL vector", fn);
   return launch_gather<T, false, EpNone>(m, qL, qG, nullptr, nullptr, nullptr, EpNone{},
                                          nullptr, as_stream(stream));
+}
+
+// Gather tiles over rows [0, nrows) of a CSR: at most kTileRows consecutive
+// rows holding at most kTileNnz entries (a longer row gets a tile of its
+// own); at least one (possibly empty) tile.  (first row, first entry) each.
+static std::vector<int2> make_tiles(const std::vector<int32_t> &rs, int64_t nrows) {
+  std::vector<int32_t> tiles;
+  tiles.push_back(0);
+  for (int64_t g = 0; g < nrows;) {
+    int64_t r = g;
+    while (r < nrows && r - g < kTileRows && rs[(size_t)r + 1] - rs[(size_t)g] <= kTileNnz) ++r;
+    if (r == g) r = g + 1;
+    tiles.push_back((int32_t)r);
+    g = r;
+  }
+  if (tiles.size() == 1) tiles.push_back(0);
+  std::vector<int2> out(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i) out[i] = make_int2(tiles[i], rs[(size_t)tiles[i]]);
+  return out;
+}
+
+template <typename V>
+static cudaError_t upload(V **d, const std::vector<V> &h, size_t pad = 0) {
+  cudaError_t e = cudaMalloc(d, sizeof(V) * (h.size() + pad + (h.empty() && !pad ? 1 : 0)));
+  if (e == cudaSuccess && !h.empty())
+    e = cudaMemcpy(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice);
+  return e;
 }
 
 }  // namespace bs
@@ -88,21 +120,21 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
       if (id >= 0) col[(size_t)fill[(size_t)id]++] = (int32_t)l;
     }
   }
-  // gather tiles: at most kTileRows consecutive rows holding at most kTileNnz
-  // CSR entries (a longer row gets a tile of its own); at least one tile
-  std::vector<int32_t> tiles;
-  tiles.push_back(0);
-  for (int64_t g = 0; g < NG;) {
-    int64_t r = g;
-    while (r < NG && r - g < kTileRows && rs[(size_t)r + 1] - rs[(size_t)g] <= kTileNnz) ++r;
-    if (r == g) r = g + 1;
-    tiles.push_back((int32_t)r);
-    g = r;
+  const std::vector<int2> tile_bounds = make_tiles(rs, NG);
+  // the fused operator's encoding and the CSR of the rows with >= 2 copies
+  std::vector<int32_t> ids_f((size_t)NL), sh_rows, sh_starts(1, 0), sh_cols;
+  for (int64_t l = 0; l < NL; ++l) {
+    const int32_t id = h_l2g[l];
+    ids_f[(size_t)l] = id < 0 ? -1 : (rs[(size_t)id + 1] - rs[(size_t)id] == 1 ? -2 - id : id);
   }
-  if (tiles.size() == 1) tiles.push_back(0);
-  std::vector<int2> tile_bounds(tiles.size());
-  for (size_t i = 0; i < tiles.size(); ++i)
-    tile_bounds[i] = make_int2(tiles[i], rs[(size_t)tiles[i]]);
+  for (int64_t g = 0; g < NG; ++g) {
+    const int32_t a = rs[(size_t)g], b = rs[(size_t)g + 1];
+    if (b - a == 1) continue;  // valence 0 rows stay here: the gather writes their zero
+    sh_rows.push_back((int32_t)g);
+    sh_cols.insert(sh_cols.end(), col.begin() + a, col.begin() + b);
+    sh_starts.push_back((int32_t)sh_cols.size());
+  }
+  const std::vector<int2> sh_tiles = make_tiles(sh_starts, (int64_t)sh_rows.size());
   // elements in the order of their smallest global index (ties keep storage
   // order); all-masked elements go last
   std::vector<int32_t> order((size_t)E);
@@ -124,7 +156,10 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
   m->NL = NL;
   m->NG = NG;
   m->nnz = nnz;
-  m->ntiles = (int64_t)tiles.size() - 1;
+  m->ntiles = (int64_t)tile_bounds.size() - 1;
+  m->nsh = (int64_t)sh_rows.size();
+  m->nnz_sh = (int64_t)sh_cols.size();
+  m->nsh_tiles = (int64_t)sh_tiles.size() - 1;
   cudaError_t e = cudaGetDevice(&m->device);
   // +4 elements of padding so 128-bit loads of the map never leave the buffer
   if (e == cudaSuccess) e = cudaMalloc(&m->d_ids, sizeof(int32_t) * (NL + 4));
@@ -144,6 +179,11 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
   if (e == cudaSuccess) e = cudaMalloc(&m->d_elem_order, sizeof(int32_t) * (E > 0 ? E : 1));
   if (e == cudaSuccess && E)
     e = cudaMemcpy(m->d_elem_order, order.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = upload(&m->d_ids_f, ids_f, 4);
+  if (e == cudaSuccess) e = upload(&m->d_sh_rows, sh_rows);
+  if (e == cudaSuccess) e = upload(&m->d_sh_starts, sh_starts);
+  if (e == cudaSuccess) e = upload(&m->d_sh_cols, sh_cols, 4);
+  if (e == cudaSuccess) e = upload(&m->d_sh_tiles, sh_tiles);
   if (e != cudaSuccess) {
     free_map(m);
     return fail(BS_ERR_CUDA, "bs_map_create: %s", cudaGetErrorString(e));

@@ -26,6 +26,14 @@ struct bs_map {
   int64_t ntiles;
   int2 *d_tiles;          // [ntiles + 1] (first row, first CSR entry) per tile
   int32_t *d_elem_order;  // [E] elements by smallest global index
+  // Fused operator (bs_op.cuh): the map re-encoded for an element kernel that
+  // writes single-copy nodes itself, and the CSR of the shared rows alone.
+  int32_t *d_ids_f;       // [NL] g if node g has != 1 copies, -2 - g if one, -1 masked
+  int64_t nsh, nnz_sh, nsh_tiles;
+  int32_t *d_sh_rows;     // [nsh] global index of each row with != 1 copies, ascending
+  int32_t *d_sh_starts;   // [nsh + 1]
+  int32_t *d_sh_cols;     // [nnz_sh] the rows' CSR entries, ascending local index
+  int2 *d_sh_tiles;       // [nsh_tiles + 1]
 };
 
 namespace bs {

@@ -10,6 +10,8 @@
 
 namespace bs {
 
+int g_op_fusion = 0;
+
 // GLL nodes on [-1, 1] (Sec. 2, eq. basis): the N+1 zeros of (1 - x^2) P_N'(x).
 // Newton on the Legendre-Vandermonde recurrence
 //   x <- x - (x P_N(x) - P_{N-1}(x)) / ((N + 1) P_N(x)),
@@ -126,6 +128,7 @@ static void free_problem(bs_problem *p) {
   cudaFree(p->d_vec);
   cudaFree(p->d_state);
   cudaFree(p->d_partials);
+  cudaFree(p->d_op_partials);
   cudaFree(p->d_f32);
   if (p->h_state) cudaFreeHost(p->h_state);
   free(p);
@@ -195,6 +198,8 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
   if (e == cudaSuccess) e = cudaMemset(p->d_state, 0, sizeof(CgState));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_partials, sizeof(double) * kMaxPartials + 256);
   if (e == cudaSuccess) e = cudaMemset(p->d_partials, 0, sizeof(double) * kMaxPartials + 256);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&p->d_op_partials, sizeof(double) * (ax_blocks(N, map->E) + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_state, sizeof(CgState));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -225,13 +230,8 @@ int bs_apply_A(const bs_problem *p, const double *x, double *Ax, void *stream) {
   if (p->map->NG == 0) return BS_OK;
   BS_ARG(x && Ax, "bs_apply_A: NULL vector");
   const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
-  cudaStream_t s = as_stream(stream);
-  if (int rc = launch_ax_local<double, true>(p->N, p->map->E, p->map->d_elem_order,
-                                             p->map->d_ids, x, p->d_ApL, p->d_tab, p->d_coef, g,
-                                             mlam, nullptr, s))
-    return rc;
-  return launch_gather<double, false, EpNone>(p->map, p->d_ApL, Ax, nullptr, nullptr, nullptr,
-                                              EpNone{}, nullptr, s);
+  return apply_A_global<double, false, EpNone>(p, false, p->d_tab, x, Ax, p->d_ApL, g, mlam,
+                                               EpNone{}, nullptr, as_stream(stream));
 }
 
 int bs_apply_A_ff(const bs_problem *p, const double *x, double *Ax, void *stream) {
@@ -239,12 +239,8 @@ int bs_apply_A_ff(const bs_problem *p, const double *x, double *Ax, void *stream
   if (p->map->NG == 0) return BS_OK;
   BS_ARG(x && Ax, "bs_apply_A_ff: NULL vector");
   const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
-  cudaStream_t s = as_stream(stream);
-  if (int rc = launch_ax_local_ff<true>(p->N, p->map->E, p->map->d_elem_order, p->map->d_ids, x,
-                                        p->d_ApL, p->d_tabff, p->d_coef, g, mlam, nullptr, s))
-    return rc;
-  return launch_gather<double, false, EpNone>(p->map, p->d_ApL, Ax, nullptr, nullptr, nullptr,
-                                              EpNone{}, nullptr, s);
+  return apply_A_global<double, false, EpNone>(p, true, p->d_tab, x, Ax, p->d_ApL, g, mlam,
+                                               EpNone{}, nullptr, as_stream(stream));
 }
 
 int bs_diag_A(const bs_problem *p, double *d_diag, void *stream) {
@@ -261,6 +257,12 @@ int bs_diag_A(const bs_problem *p, double *d_diag, void *stream) {
   }
   return launch_gather<double, false, EpNone>(p->map, p->d_ApL, d_diag, nullptr, nullptr,
                                               nullptr, EpNone{}, nullptr, s);
+}
+
+int bs_operator_fusion(int32_t mode) {
+  const int prev = g_op_fusion;
+  if (mode >= 0) g_op_fusion = mode ? 1 : 0;
+  return prev;
 }
 
 }  // extern "C"

@@ -13,6 +13,20 @@
 // element and walks k, keeping the column in registers; the element sits in
 // shared memory.  Reading the input through the map (GATHER_IN) fuses the
 // scatter Z p into the same pass, so the N_L-sized Z p is never stored.
+//
+// Fused form (FUSED): the map comes re-encoded (bs_map::d_ids_f) so that the
+// kernel knows which global nodes have a single local copy -- element
+// interiors and the faces on the natural boundary, 63% of the nodes at
+// N = 7.  For those, Z^T is the identity: the kernel writes (A p)_g = +0 +
+// (A_L Z p)_l straight into the global output and adds p_g (A p)_g to a
+// per-block partial of p.Ap; only the shared nodes' local values go to the
+// N_L buffer, for a gather over the shared rows alone.  The result is
+// bitwise that of the unfused operator (a one-term row sum is +0 + v).
+// Measured slower on GB300 (N = 7 on 48^3: 1.365 vs 1.244 ms per A p with
+// the float-float kernel, 3.54 vs 3.44 ms in FP64): in the user's global
+// numbering the single-copy nodes come in runs of N - 1 doubles and the
+// shared rows between them, so both kernels write partial sectors of A p,
+// which costs more than the N_L round trip saved.  Off by default.
 #pragma once
 
 #include "bs_gather.cuh"
@@ -43,15 +57,20 @@ struct OpShape {
 // (masked nodes read as 0); else in is element-local.  g = h/2 (the
 // c-independent stiffness factor), mlam = lambda (h/2)^3.  Elements visited
 // in `order` (sorted by smallest global index) meet their neighbours' reads
-// in L2.  s_u holds EPB * NQ^3 values, s_K NQ^2, s_w NQ.
-template <typename T, int NQ, bool GATHER_IN>
+// in L2.  s_u holds EPB * NQ^3 values, s_K NQ^2, s_w NQ.  FUSED (with
+// GATHER_IN, ids the fused encoding): single-copy nodes go to outG, with
+// p_g (A p)_g added to acc, shared ones to out; masked ones nowhere.
+template <typename T, int NQ, bool GATHER_IN, bool FUSED = false>
 __device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
                                             const int32_t *__restrict__ order,
                                             const int32_t *__restrict__ ids,
                                             const T *__restrict__ in, T *__restrict__ out,
                                             const OpTab<T> *__restrict__ tab,
                                             const double *__restrict__ coef, T g, T mlam,
-                                            T *s_u_all, T *s_K, T *s_w) {
+                                            T *s_u_all, T *s_K, T *s_w,
+                                            T *__restrict__ outG = nullptr,
+                                            Acc<T> *acc = nullptr) {
+  static_assert(!FUSED || GATHER_IN, "the fused operator reads its input through the map");
   using S = OpShape<NQ>;
   __syncthreads();  // the shared buffers may still be in use by a previous call
   for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) s_K[t] = tab->K[(t / NQ) * NQ + t % NQ];
@@ -64,12 +83,18 @@ __device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
   T *u = s_u_all + (le < S::EPB ? le : 0) * S::NP;
   T ureg[NQ];
+  int32_t gid[FUSED ? NQ : 1];  // fused: the encoded id of each node of the column
   if (active) {
     const int64_t base = e * S::NP + ij;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
       T v;
-      if (GATHER_IN) {
+      if (FUSED) {
+        const int32_t id = __ldcs(ids + base + k * S::NQ2);
+        gid[k] = id;
+        const int32_t gg = id >= 0 ? id : -2 - id;
+        v = id != -1 ? in[gg] : T(0);
+      } else if (GATHER_IN) {
         const int32_t id = __ldcs(ids + base + k * S::NQ2);
         v = id >= 0 ? in[id] : T(0);
       } else {
@@ -99,36 +124,72 @@ __device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
     stiff = fmaT(wi * wk, as, stiff);
     stiff = fmaT(wij, at, stiff);
     const T mass = mlam * (wij * wk) * ureg[k];
-    __stcs(out + e * S::NP + ij + k * S::NQ2, fmaT(cg, stiff, mass));
+    const T res = fmaT(cg, stiff, mass);
+    if (FUSED) {
+      const int32_t id = gid[FUSED ? k : 0];
+      if (id >= 0) {
+        __stcs(out + e * S::NP + ij + k * S::NQ2, res);
+      } else if (id != -1) {
+        const T v = plus_zero(res);
+        __stcs(outG + (-2 - id), v);
+        acc->add(ureg[k], v);
+      }
+    } else {
+      __stcs(out + e * S::NP + ij + k * S::NQ2, res);
+    }
   }
 }
 
-template <typename T, int NQ, bool GATHER_IN>
+template <typename T, int NQ, bool GATHER_IN, bool FUSED>
 __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
     k_ax_local(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
                const T *__restrict__ in, T *__restrict__ out, const OpTab<T> *__restrict__ tab,
-               const double *__restrict__ coef, T g, T mlam, const CgState *st) {
+               const double *__restrict__ coef, T g, T mlam, const CgState *st,
+               T *__restrict__ outG, double *__restrict__ partials) {
   using S = OpShape<NQ>;
   __shared__ T s_u[S::EPB * S::NP];
   __shared__ T s_K[NQ * NQ];
   __shared__ T s_w[NQ];
   if (cg_halted(st)) return;
-  ax_elements<T, NQ, GATHER_IN>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out, tab, coef,
-                                g, mlam, s_u, s_K, s_w);
+  Acc<T> acc;
+  ax_elements<T, NQ, GATHER_IN, FUSED>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out,
+                                       tab, coef, g, mlam, s_u, s_K, s_w, outG, &acc);
+  if (FUSED && partials) {
+    const double part = block_sum<S::THREADS>(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = part;
+  }
 }
 
-template <typename T, bool GATHER_IN>
+// Blocks of the element kernels for E elements of degree N (the fused
+// operator's partials hold one double per block).
+inline int64_t ax_blocks(int N, int64_t E) {
+  switch (N + 1) {
+#define BS_AXB(NQ) \
+  case NQ:         \
+    return (E + OpShape<NQ>::EPB - 1) / OpShape<NQ>::EPB;
+    BS_AXB(2) BS_AXB(3) BS_AXB(4) BS_AXB(5) BS_AXB(6) BS_AXB(7) BS_AXB(8) BS_AXB(9)
+    BS_AXB(10) BS_AXB(11) BS_AXB(12) BS_AXB(13) BS_AXB(14) BS_AXB(15) BS_AXB(16)
+#undef BS_AXB
+    default:
+      return 0;
+  }
+}
+
+// FUSED: ids is the fused encoding, outG the global output, partials (or
+// NULL: no dot product) ax_blocks(N, E) doubles.
+template <typename T, bool GATHER_IN, bool FUSED = false>
 int launch_ax_local(int N, int64_t E, const int32_t *order, const int32_t *ids, const T *in,
                     T *out,
                     const OpTab<T> *tab, const double *coef, T g, T mlam,
-                    const CgState *st, cudaStream_t s) {
+                    const CgState *st, cudaStream_t s, T *outG = nullptr,
+                    double *partials = nullptr) {
   if (E == 0) return BS_OK;
 #define BS_AX_CASE(NQ)                                                                   \
   case NQ: {                                                                             \
     using Sh = OpShape<NQ>;                                                              \
     const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                    \
-    k_ax_local<T, NQ, GATHER_IN><<<(unsigned)grid, Sh::THREADS, 0, s>>>(                 \
-        E, order, ids, in, out, tab, coef, g, mlam, st);                                 \
+    k_ax_local<T, NQ, GATHER_IN, FUSED><<<(unsigned)grid, Sh::THREADS, 0, s>>>(          \
+        E, order, ids, in, out, tab, coef, g, mlam, st, outG, partials);                 \
     break;                                                                               \
   }
   switch (N + 1) {
@@ -173,6 +234,7 @@ struct bs_problem {
   double *d_vec;                  // 6 x [NG]: r, p, Ap, z, dinv, spare
   bs::CgState *d_state;
   double *d_partials;             // [kMaxPartials]
+  double *d_op_partials;          // [ax_blocks(N, E)] the fused operator's block partials
   unsigned int *d_counter;
   bs::CgState *h_state;           // pinned host mirror for convergence checks
   cudaStream_t cap_stream;        // private stream for graph capture

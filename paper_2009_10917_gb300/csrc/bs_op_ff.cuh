@@ -23,6 +23,8 @@
 // breakdown.
 #pragma once
 
+#include <type_traits>
+
 #include "bs_op.cuh"
 
 namespace bs {
@@ -100,8 +102,9 @@ __device__ __forceinline__ void ff_dot_acc(FF &acc, double &dacc, double a, doub
   }
 }
 
-// out = A_L in on elements slot0 .. slot0 + EPB - 1, as ax_elements.
-template <int NQ, bool GATHER_IN>
+// out = A_L in on elements slot0 .. slot0 + EPB - 1, as ax_elements
+// (FUSED likewise; the dot product reads p_g again, from cache, in FP64).
+template <int NQ, bool GATHER_IN, bool FUSED = false>
 __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
                                                const int32_t *__restrict__ order,
                                                const int32_t *__restrict__ ids,
@@ -110,7 +113,10 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
                                                const OpTabFF *__restrict__ tab,
                                                const double *__restrict__ coef, double g,
                                                double mlam, float *s_uh_all, float *s_ul_all,
-                                               float *s_K, float *s_w) {
+                                               float *s_K, float *s_w,
+                                               double *__restrict__ outG = nullptr,
+                                               Acc<double> *acc = nullptr) {
+  static_assert(!FUSED || GATHER_IN, "the fused operator reads its input through the map");
   using S = OpShape<NQ>;
   constexpr int NQ2 = NQ * NQ;
   float *s_Kh = s_K, *s_Kl = s_K + NQ2, *s_Wh = s_K + 2 * NQ2, *s_Wl = s_K + 3 * NQ2;
@@ -135,12 +141,17 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
   float *uh = s_uh_all + (le < S::EPB ? le : 0) * S::NP;
   float *ul = s_ul_all + (le < S::EPB ? le : 0) * S::NP;
   float rh[NQ], rl[NQ];
+  int32_t gid[FUSED ? NQ : 1];
   if (active) {
     const int64_t base = e * S::NP + ij;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
       double v;
-      if (GATHER_IN) {
+      if (FUSED) {
+        const int32_t id = __ldcs(ids + base + k * NQ2);
+        gid[k] = id;
+        v = id != -1 ? in[id >= 0 ? id : -2 - id] : 0.0;
+      } else if (GATHER_IN) {
         const int32_t id = __ldcs(ids + base + k * NQ2);
         v = id >= 0 ? in[id] : 0.0;
       } else {
@@ -182,37 +193,56 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
     FF o{0.f, 0.f};
     ff_fma(o, cg.hi, cg.lo, t.hi, t.lo);
     ff_fma(o, mk.hi, mk.lo, rh[k], rl[k]);
-    __stcs(out + e * S::NP + ij + k * NQ2, ff_widen(o.hi) + ff_widen(o.lo));
+    const double res = ff_widen(o.hi) + ff_widen(o.lo);
+    if (FUSED) {
+      const int32_t id = gid[FUSED ? k : 0];
+      if (id >= 0) {
+        __stcs(out + e * S::NP + ij + k * NQ2, res);
+      } else if (id != -1) {
+        const double v = plus_zero(res);
+        __stcs(outG + (-2 - id), v);
+        acc->add(__ldg(in + (-2 - id)), v);
+      }
+    } else {
+      __stcs(out + e * S::NP + ij + k * NQ2, res);
+    }
   }
 }
 
-template <int NQ, bool GATHER_IN>
+template <int NQ, bool GATHER_IN, bool FUSED>
 __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
     k_ax_local_ff(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
                   const double *__restrict__ in, double *__restrict__ out,
                   const OpTabFF *__restrict__ tab, const double *__restrict__ coef, double g,
-                  double mlam, const CgState *st) {
+                  double mlam, const CgState *st, double *__restrict__ outG,
+                  double *__restrict__ partials) {
   using S = OpShape<NQ>;
   __shared__ float s_uh[S::EPB * S::NP];
   __shared__ float s_ul[S::EPB * S::NP];
   __shared__ float s_K[4 * NQ * NQ];
   __shared__ float s_w[2 * NQ];
   if (cg_halted(st)) return;
-  ax_elements_ff<NQ, GATHER_IN>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out, tab, coef,
-                                g, mlam, s_uh, s_ul, s_K, s_w);
+  Acc<double> acc;
+  ax_elements_ff<NQ, GATHER_IN, FUSED>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out,
+                                       tab, coef, g, mlam, s_uh, s_ul, s_K, s_w, outG, &acc);
+  if (FUSED && partials) {
+    const double part = block_sum<S::THREADS>(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = part;
+  }
 }
 
-template <bool GATHER_IN>
+template <bool GATHER_IN, bool FUSED = false>
 int launch_ax_local_ff(int N, int64_t E, const int32_t *order, const int32_t *ids,
                        const double *in, double *out, const OpTabFF *tab, const double *coef,
-                       double g, double mlam, const CgState *st, cudaStream_t s) {
+                       double g, double mlam, const CgState *st, cudaStream_t s,
+                       double *outG = nullptr, double *partials = nullptr) {
   if (E == 0) return BS_OK;
 #define BS_AXFF_CASE(NQ)                                                              \
   case NQ: {                                                                          \
     using Sh = OpShape<NQ>;                                                           \
     const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                 \
-    k_ax_local_ff<NQ, GATHER_IN><<<(unsigned)grid, Sh::THREADS, 0, s>>>(              \
-        E, order, ids, in, out, tab, coef, g, mlam, st);                              \
+    k_ax_local_ff<NQ, GATHER_IN, FUSED><<<(unsigned)grid, Sh::THREADS, 0, s>>>(       \
+        E, order, ids, in, out, tab, coef, g, mlam, st, outG, partials);              \
     break;                                                                            \
   }
   switch (N + 1) {
@@ -237,6 +267,45 @@ int launch_ax_local_ff(int N, int64_t E, const int32_t *order, const int32_t *id
 #undef BS_AXFF_CASE
   BS_LAUNCH_CHECK();
   return BS_OK;
+}
+
+// 1: A p through the fused element kernel and the gather of the shared rows;
+// 0 (the default): element kernel, then the gather of every row.
+extern int g_op_fusion;
+
+// Ap = A p for a global p (FP64 or FP32 tables; ff: the float-float element
+// kernel, FP64 only).  DOT: ep(p . Ap), reduced in the gather's pass (and,
+// fused, in the element kernel's epilogue for the single-copy nodes).
+template <typename T, bool DOT, class Ep>
+int apply_A_global(const bs_problem *P, bool ff, const OpTab<T> *tab, const T *p, T *Ap, T *ApL,
+                   T g, T mlam, Ep ep, const CgState *st, cudaStream_t s) {
+  const bs_map *m = P->map;
+  const bool fused = g_op_fusion != 0;
+  const int32_t *ids = fused ? m->d_ids_f : m->d_ids;
+  double *opp = fused && DOT ? P->d_op_partials : nullptr;
+  int rc;
+  if constexpr (std::is_same<T, double>::value) {
+    if (ff)
+      rc = fused ? launch_ax_local_ff<true, true>(P->N, m->E, m->d_elem_order, ids, p, ApL,
+                                                  P->d_tabff, P->d_coef, g, mlam, st, s, Ap, opp)
+                 : launch_ax_local_ff<true>(P->N, m->E, m->d_elem_order, ids, p, ApL, P->d_tabff,
+                                            P->d_coef, g, mlam, st, s);
+    else
+      rc = fused ? launch_ax_local<T, true, true>(P->N, m->E, m->d_elem_order, ids, p, ApL, tab,
+                                                  P->d_coef, g, mlam, st, s, Ap, opp)
+                 : launch_ax_local<T, true>(P->N, m->E, m->d_elem_order, ids, p, ApL, tab,
+                                            P->d_coef, g, mlam, st, s);
+  } else {
+    if (ff) return fail(BS_ERR_ARG, "the float-float operator is FP64 only");
+    rc = fused ? launch_ax_local<T, true, true>(P->N, m->E, m->d_elem_order, ids, p, ApL, tab,
+                                                P->d_coef, g, mlam, st, s, Ap, opp)
+               : launch_ax_local<T, true>(P->N, m->E, m->d_elem_order, ids, p, ApL, tab,
+                                          P->d_coef, g, mlam, st, s);
+  }
+  if (rc) return rc;
+  return launch_gather_rows<T, DOT, Ep>(m, fused, ApL, Ap, DOT ? p : nullptr, P->d_partials,
+                                        P->d_counter, opp, opp ? ax_blocks(P->N, m->E) : 0, ep,
+                                        st, s);
 }
 
 }  // namespace bs

@@ -18,7 +18,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "bs_op.cuh"
+#include "bs_op_ff.cuh"
 
 namespace bs {
 
@@ -121,11 +121,8 @@ static int f32_iteration(const bs_problem *P, cudaStream_t s) {
   float *ApL = reinterpret_cast<float *>(P->d_ApL);
   const float g = (float)(0.5 * P->h);
   const float mlam = (float)(P->lambda * 0.125 * P->h * P->h * P->h);
-  int rc = launch_ax_local<float, true>(P->N, m->E, m->d_elem_order, m->d_ids, v.p, ApL,
-                                        P->d_tabf, P->d_coef, g, mlam, st, s);
-  if (rc) return rc;
-  rc = launch_gather<float, true, EpAlphaF>(m, ApL, v.Ap, v.p, P->d_partials, P->d_counter,
-                                            EpAlphaF{st}, st, s);
+  int rc = apply_A_global<float, true, EpAlphaF>(P, false, P->d_tabf, v.p, v.Ap, ApL, g, mlam,
+                                                  EpAlphaF{st}, st, s);
   if (rc) return rc;
   rc = launch_cg_update<float, EpBetaF>(m->NG, Scalar<float>{0.f, &st->alpha_f}, v.p, v.Ap, v.d,
                                         v.r, P->d_partials, P->d_counter, EpBetaF{st}, st, s);
@@ -135,7 +132,8 @@ static int f32_iteration(const bs_problem *P, cudaStream_t s) {
 }
 
 static int capture_f32(bs_problem *P, int chunk) {
-  const void *key[4] = {nullptr, (const void *)(intptr_t)2, (const void *)(intptr_t)chunk,
+  const void *key[4] = {nullptr, (const void *)(intptr_t)(2 | (g_op_fusion ? 4 : 0)),
+                        (const void *)(intptr_t)chunk,
                         (const void *)P->map};
   if (P->graph && memcmp(key, P->graph_key, sizeof(key)) == 0) return BS_OK;
   if (P->graph) {
@@ -204,11 +202,8 @@ extern "C" int bs_cg_solve_refined_f32(const bs_problem *Pc, const double *b, do
   const int grid = stream_grid(NG, 1, kReduceBlock, 6);
   for (;;) {
     // outer residual in FP64
-    rc = launch_ax_local<double, true>(P->N, m->E, m->d_elem_order, m->d_ids, x, P->d_ApL,
-                                       P->d_tab, P->d_coef, g, mlam, nullptr, s);
-    if (!rc)
-      rc = launch_gather<double, false, EpNone>(m, P->d_ApL, Ax, nullptr, nullptr, nullptr,
-                                                EpNone{}, nullptr, s);
+    rc = apply_A_global<double, false, EpNone>(P, false, P->d_tab, x, Ax, P->d_ApL, g, mlam,
+                                               EpNone{}, nullptr, s);
     if (rc) break;
     k_residual<<<grid, kReduceBlock, 0, s>>>(NG, b, Ax, r64, v.r, P->d_partials, P->d_counter,
                                              scal);
