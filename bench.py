@@ -363,9 +363,11 @@ def operator_times(P, p, reps=20):
 def cg_section(args):
     """Time to tolerance of Algorithm 1 on the GLL Helmholtz operator
     (lambda = 1, b uniform[-1, 1)): plain FP64 CG to 1e-8, the same with the
-    float-float element operator, and FP32-storage CG inside FP64 iterative
-    refinement to 1e-8 (FP64 true residual), each after one untimed warm-up
-    solve; plus the small configuration's 50 fixed FP64 iterations.  Wall
+    float-float element operator, FP32-storage CG inside FP64 iterative
+    refinement to 1e-8 (FP64 true residual), and the FP64 and float-float
+    solves with the vectors in scattered storage (Sec. 3), each after one
+    untimed warm-up solve; plus the small configuration's 50 fixed FP64
+    iterations and the algorithmic bytes per iteration of both storages.  Wall
     time measured by the library around each solve (host clock, stream
     synchronised); every result's true residual is recomputed with the FP64
     operator."""
@@ -389,7 +391,13 @@ def cg_section(args):
                 ("fp64_cg_ff_operator",
                  lambda: P.cg(b, tol=1e-8, maxit=100000,
                               flags=bs.BS_CG_GRAPH | bs.BS_CG_FF_OPERATOR)),
-                ("fp32_ir_1e-8", lambda: P.cg_refined_f32(b, tol=1e-8, flags=bs.BS_CG_GRAPH))]
+                ("fp32_ir_1e-8", lambda: P.cg_refined_f32(b, tol=1e-8, flags=bs.BS_CG_GRAPH)),
+                ("fp64_cg_scattered",
+                 lambda: P.cg(b, tol=1e-8, maxit=100000,
+                              flags=bs.BS_CG_GRAPH | bs.BS_CG_SCATTERED)),
+                ("fp64_cg_ff_operator_scattered",
+                 lambda: P.cg(b, tol=1e-8, maxit=100000,
+                              flags=bs.BS_CG_GRAPH | bs.BS_CG_FF_OPERATOR | bs.BS_CG_SCATTERED))]
         bn = torch.linalg.norm(b).item()
         for name, fn in runs:
             fn()
@@ -418,6 +426,12 @@ def cg_section(args):
         for k in ("fp64_cg_ff_operator", "fp32_ir_1e-8"):
             res[f"speedup_{k}_vs_fp64_at_1e-8"] = round(
                 res["fp64_cg"]["seconds"] / res[k]["seconds"], 3)
+        # scattered (N_L) against global (N_G) storage of the CG vectors
+        res["bytes_per_iteration"] = {"global": 24 * m.NL + 100 * m.NG,
+                                      "scattered": 122 * m.NL + 20 * m.NG}
+        for k, g in (("fp64_cg_scattered", "fp64_cg"),
+                     ("fp64_cg_ff_operator_scattered", "fp64_cg_ff_operator")):
+            res[f"time_ratio_{k}_vs_global"] = round(res[k]["seconds"] / res[g]["seconds"], 3)
         out[label] = res
         del P, Z, b
         torch.cuda.empty_cache()

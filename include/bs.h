@@ -201,7 +201,8 @@ enum {
   BS_CG_GRAPH = 4,       /* replay the iteration as a captured CUDA graph  */
   BS_CG_X0 = 8,          /* x holds the initial guess (else x0 = 0)        */
   BS_CG_REFINED_F32 = 32, /* batched: FP32 inner CG, FP64 refinement       */
-  BS_CG_FF_OPERATOR = 256 /* the float-float operator of bs_apply_A_ff      */
+  BS_CG_FF_OPERATOR = 256, /* the float-float operator of bs_apply_A_ff     */
+  BS_CG_SCATTERED = 512     /* bs_cg_solve: vectors in scattered storage    */
 };
 
 typedef struct {
@@ -224,7 +225,15 @@ typedef struct {
  * bs_apply_A_ff; vectors, reductions and updates stay FP64; the solve runs
  * on the system scaled by the power of two that brings the RMS of b near 1,
  * exactly undone on x, so the operator's 2^-102 floor is relative to b;
- * d_hist then holds the scaled r.r).  Synchronises
+ * d_hist then holds the scaled r.r), BS_CG_SCATTERED (the scattered form
+ * that Sec. 3 sets against global storage: Z applied to both sides, every
+ * CG vector kept as its N_L-sized scattered copy v_L = Z v_G, A p formed as
+ * Z Z^T A_L p_L -- element kernel on contiguous local data, gather (BS6),
+ * scatter (BS7) -- and each inner product summed over one copy of every
+ * global node, the lowest local index, so that it equals the global one
+ * term for term; b and x stay N_G vectors at the boundary; 122 N_L + 20 N_G
+ * bytes per iteration against 24 N_L + 100 N_G in global storage, 1.5 times
+ * as many at N = 7).  Synchronises
  * `stream` before returning; info (host) may be NULL.  Returns
  * BS_ERR_NOT_CONVERGED if maxit is reached without BS_CG_FIXED_ITERS,
  * BS_ERR_BREAKDOWN on p.Ap <= 0. */

@@ -34,6 +34,7 @@ BS_CG_GRAPH = 4
 BS_CG_X0 = 8
 BS_CG_REFINED_F32 = 32
 BS_CG_FF_OPERATOR = 256
+BS_CG_SCATTERED = 512
 BS_MLP_BF16X3 = 1
 BS_MLP_ODD = 2
 BS_FPCG_ODD = 64

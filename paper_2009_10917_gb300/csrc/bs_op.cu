@@ -130,6 +130,8 @@ static void free_problem(bs_problem *p) {
   cudaFree(p->d_partials);
   cudaFree(p->d_op_partials);
   cudaFree(p->d_f32);
+  cudaFree(p->d_Lvec);
+  cudaFree(p->d_owner);
   if (p->h_state) cudaFreeHost(p->h_state);
   free(p);
 }

@@ -241,4 +241,6 @@ struct bs_problem {
   cudaGraphExec_t graph;          // cached CG chunk graph
   const void *graph_key[4];       // (x, variant, chunk, map) the graph was made for
   float *d_f32;                   // 4 x [NG + 8] FP32 vectors (refined solver), lazily
+  double *d_Lvec;                 // 6 x [NL + 2 rounded up to even] scattered CG vectors, lazily
+  uint8_t *d_owner;               // [NL + 16] 1 at the lowest local copy of each node, lazily
 };
