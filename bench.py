@@ -331,32 +331,36 @@ def run_ours(args):
 
 def operator_times(P, p, reps=20):
     """Device time of one A p (ms, CUDA events over reps calls after three
-    warm-up calls): FP64 and float-float element kernels, each fused (single-
-    copy nodes written by the element kernel, gather of the shared rows) and
-    unfused (element kernel, gather of every row)."""
+    warm-up calls) in each operator mode: the FP64 element kernel in the
+    even-odd form (the default) and direct, each unfused (element kernel,
+    gather of every row) and fused (single-copy nodes written by the element
+    kernel, gather of the shared rows); the float-float kernel (always
+    direct) unfused and fused."""
     import torch
 
     from paper_2009_10917_gb300 import bs
     out = {}
     Ap = torch.empty_like(p)
-    prev = bs.operator_fusion(-1)
+    prev = bs.operator_mode(-1)
+    cases = [("fp64_evenodd", 0, P.apply_A), ("fp64_direct", bs.BS_OP_DIRECT, P.apply_A),
+             ("fp64_evenodd_fused", bs.BS_OP_FUSED, P.apply_A),
+             ("fp64_direct_fused", bs.BS_OP_FUSED | bs.BS_OP_DIRECT, P.apply_A),
+             ("ff", 0, P.apply_A_ff), ("ff_fused", bs.BS_OP_FUSED, P.apply_A_ff)]
     try:
-        for fused in (1, 0):
-            bs.operator_fusion(fused)
-            for name, fn in (("fp64", P.apply_A), ("ff", P.apply_A_ff)):
-                for _ in range(3):
-                    fn(p, Ap)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record()
-                for _ in range(reps):
-                    fn(p, Ap)
-                e1.record()
-                torch.cuda.synchronize()
-                out[f"{name}_{'fused' if fused else 'unfused'}"] = round(
-                    e0.elapsed_time(e1) / reps, 4)
+        for name, mode, fn in cases:
+            bs.operator_mode(mode)
+            for _ in range(3):
+                fn(p, Ap)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                fn(p, Ap)
+            e1.record()
+            torch.cuda.synchronize()
+            out[name] = round(e0.elapsed_time(e1) / reps, 4)
     finally:
-        bs.operator_fusion(prev)
+        bs.operator_mode(prev)
     return out
 
 

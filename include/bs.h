@@ -179,19 +179,29 @@ int bs_diag_A(const bs_problem *prob, double *d_diag, void *stream);
  * bs_apply_A's. */
 int bs_apply_A_ff(const bs_problem *prob, const double *p, double *Ap, void *stream);
 
-/* How A p is formed, process-wide, by bs_apply_A, bs_apply_A_ff and every
- * solver but the batched one.  1: fused -- a global node with a single local
- * copy (an element interior, a face on the natural boundary) needs no
- * gather, so the element kernel writes its value into Ap itself and adds its
- * term of p.Ap in the same pass; only nodes with several copies go through
- * the N_L buffer and a gather over their rows alone.  0 (the default): the
- * element kernel writes every local value and the gather (BS6) sums every
- * row.  Ap is bitwise the same either way (a one-copy row sums to +0 + v);
- * p.Ap differs only by summation order.  The fused form is measured slower
- * on GB300 (partial-sector writes into Ap; N = 7 on 48^3: 1.37 vs 1.24 ms
- * per float-float A p).  Returns the previous mode; a negative value only
- * queries it.  Not thread-safe against solves in flight. */
-int bs_operator_fusion(int32_t mode);
+/* How A p is formed, process-wide, by bs_apply_A, bs_apply_local,
+ * bs_apply_A_ff and every solver but the batched one; mode is a set of bits
+ * (0, the default, is the fastest measured form):
+ *  BS_OP_FUSED: a global node with a single local copy (an element
+ *   interior, a face on the natural boundary) needs no gather, so the
+ *   element kernel writes its value into Ap itself and adds its term of p.Ap
+ *   in the same pass; only nodes with several copies go through the N_L
+ *   buffer and a gather over their rows alone.  Without it the element
+ *   kernel writes every local value and the gather (BS6) sums every row.  Ap
+ *   is bitwise the same either way (a one-copy row sums to +0 + v); p.Ap
+ *   differs only by summation order.  Measured slower on GB300
+ *   (partial-sector writes into Ap; N = 7 on 48^3: 1.37 vs 1.24 ms per
+ *   float-float A p).
+ *  BS_OP_DIRECT: the FP64 and FP32 element kernels contract with the full
+ *   1-D stiffness K = D^T W D (3 (N+1) fused multiply-adds per node).
+ *   Without it, for odd N <= 9, they use the even-odd form of the
+ *   centrosymmetric W^-1 K (Solomonoff's decomposition; half-length
+ *   contractions, about a quarter fewer FP64 operations per node); results
+ *   differ by rounding only.  The float-float kernel is always direct.
+ * Returns the previous mode; a negative value only queries it.  Not
+ * thread-safe against solves in flight. */
+enum { BS_OP_FUSED = 1, BS_OP_DIRECT = 2 };
+int bs_operator_mode(int32_t mode);
 
 /* ------------------------------------------------------------ CG */
 

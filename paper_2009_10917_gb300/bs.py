@@ -35,6 +35,8 @@ BS_CG_X0 = 8
 BS_CG_REFINED_F32 = 32
 BS_CG_FF_OPERATOR = 256
 BS_CG_SCATTERED = 512
+BS_OP_FUSED = 1
+BS_OP_DIRECT = 2
 BS_MLP_BF16X3 = 1
 BS_MLP_ODD = 2
 BS_FPCG_ODD = 64
@@ -102,14 +104,24 @@ _SIGS = {
                                                ctypes.POINTER(CgInfo), _vp]),
     "bs_cg_solve_batched": (ctypes.c_int, [_i32, _vp, _vp, _vp, _d, _i32, _i32,
                                            ctypes.POINTER(CgInfo), _vp]),
-    "bs_operator_fusion": (ctypes.c_int, [_i32]),
+    "bs_operator_mode": (ctypes.c_int, [_i32]),
 }
 
 
-def operator_fusion(mode=-1):
-    """bs_operator_fusion: 1 fused A p, 0 element kernel + full gather (the
-    default); returns the previous mode (-1: query only)."""
-    return lib().bs_operator_fusion(int(mode))
+def operator_mode(mode=-1):
+    """bs_operator_mode: bits BS_OP_FUSED, BS_OP_DIRECT (0, the default:
+    unfused, even-odd element kernels); returns the previous mode (-1: query
+    only)."""
+    return lib().bs_operator_mode(int(mode))
+
+
+def operator_fusion(on=-1):
+    """Set (1) or clear (0) BS_OP_FUSED, keeping the other bits; returns the
+    previous state of the bit (-1: query only)."""
+    prev = operator_mode(-1)
+    if on >= 0:
+        operator_mode((prev & ~BS_OP_FUSED) | (BS_OP_FUSED if on else 0))
+    return 1 if prev & BS_OP_FUSED else 0
 
 
 def library_path() -> str:

@@ -11,6 +11,7 @@
 namespace bs {
 
 int g_op_fusion = 0;
+int g_op_evenodd = 1;
 
 // GLL nodes on [-1, 1] (Sec. 2, eq. basis): the N+1 zeros of (1 - x^2) P_N'(x).
 // Newton on the Legendre-Vandermonde recurrence
@@ -172,6 +173,21 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
     hi = (float)v;
     lo = (float)(v - (double)hi);
   };
+  if (Nq % 2 == 0) {  // even-odd halves of W^-1 K, centrosymmetrised
+    const int hq = Nq / 2;
+    auto kh = [&](int a, int m) {
+      return 0.5 * (K[a * Nq + m] / w[a] + K[(Nq - 1 - a) * Nq + (Nq - 1 - m)] / w[Nq - 1 - a]);
+    };
+    for (int a = 0; a < hq; ++a)
+      for (int m = 0; m < hq; ++m) {
+        const double e = 0.5 * (kh(a, m) + kh(a, Nq - 1 - m));
+        const double o = 0.5 * (kh(a, m) - kh(a, Nq - 1 - m));
+        tab.Ee[a * hq + m] = e;
+        tab.Eo[a * hq + m] = o;
+        tabf.Ee[a * hq + m] = (float)e;
+        tabf.Eo[a * hq + m] = (float)o;
+      }
+  }
   for (int i = 0; i < Nq; ++i) {
     tab.w[i] = w[i];
     tabf.w[i] = (float)w[i];
@@ -261,9 +277,12 @@ int bs_diag_A(const bs_problem *p, double *d_diag, void *stream) {
                                               nullptr, EpNone{}, nullptr, s);
 }
 
-int bs_operator_fusion(int32_t mode) {
-  const int prev = g_op_fusion;
-  if (mode >= 0) g_op_fusion = mode ? 1 : 0;
+int bs_operator_mode(int32_t mode) {
+  const int prev = (g_op_fusion ? BS_OP_FUSED : 0) | (g_op_evenodd ? 0 : BS_OP_DIRECT);
+  if (mode >= 0) {
+    g_op_fusion = (mode & BS_OP_FUSED) ? 1 : 0;
+    g_op_evenodd = (mode & BS_OP_DIRECT) ? 0 : 1;
+  }
   return prev;
 }
 

@@ -40,6 +40,10 @@ template <typename T>
 struct OpTab {
   T K[kMaxNq * kMaxNq];  // K[i*Nq + m] = (D^T W D)_im
   T w[kMaxNq];           // GLL weights
+  // Even-odd halves of Kh = W^-1 K (centrosymmetric; even Nq only), h = Nq/2:
+  // Ee[a*h + m] = (Kh_am + Kh_a,Nq-1-m) / 2, Eo[a*h + m] = (Kh_am - Kh_a,Nq-1-m) / 2.
+  T Ee[(kMaxNq / 2) * (kMaxNq / 2)];
+  T Eo[(kMaxNq / 2) * (kMaxNq / 2)];
 };
 
 template <int NQ>
@@ -140,6 +144,194 @@ __device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
   }
 }
 
+// ---------------------------------------------------------------- even-odd form
+//
+// The GLL nodes are symmetric about 0, so Kh = W^-1 K (K = D^T W D) is
+// centrosymmetric: Kh_{N-a, N-m} = Kh_{a m}.  With e_m = u_m + u_{N-m} and
+// o_m = u_m - u_{N-m} (m < h = Nq/2; Solomonoff's even-odd decomposition of a
+// spectral differentiation matrix), one pair of outputs of a 1-D contraction
+// costs two half-length sums,
+//   (Kh u)_a = sum_m Ee_am e_m + sum_m Eo_am o_m,
+//   (Kh u)_{N-a} = sum_m Ee_am e_m - sum_m Eo_am o_m,
+// and, because stiffness and mass both carry w_i w_j w_k,
+//   (A_L u)_ijk = w_i w_j w_k (c (h/2) [(Kh u)_r + (Kh u)_s + (Kh u)_t] + lambda (h/2)^3 u_ijk).
+// About 24 FP64 operations per node instead of 32 (the element kernel is
+// FP64-pipe bound on GB300).  Even Nq only, up to 10.  Per element: the
+// column pairs along r and along s get their e/o values computed once into
+// shared memory; then each thread contracts one output pair along r (threads
+// with i < h) or along s (the others), and, from its own column in registers,
+// all outputs along t; a last pass sums the three per node.
+template <int NQ>
+struct EoShape {
+  static constexpr int H = NQ / 2;
+  static constexpr int NQ2 = NQ * NQ;
+  static constexpr int NP = NQ * NQ2;
+  static constexpr int EPB = NQ2 >= 128 ? 1 : 128 / NQ2;  // elements per block
+  static constexpr int THREADS = ((EPB * NQ2 + 31) / 32) * 32;
+  static constexpr int SMEM = EPB * 4 * NP + 2 * H * H + NQ;  // values of T
+};
+template <int NQ>
+constexpr bool use_eo() {
+  return NQ % 2 == 0 && NQ <= 10;
+}
+
+// As ax_elements (same arguments, FUSED likewise), by a block of
+// EoShape<NQ>::THREADS threads; smem holds EoShape<NQ>::SMEM values.
+template <typename T, int NQ, bool GATHER_IN, bool FUSED>
+__device__ __forceinline__ void ax_elements_eo(int64_t slot0, int64_t E,
+                                               const int32_t *__restrict__ order,
+                                               const int32_t *__restrict__ ids,
+                                               const T *__restrict__ in, T *__restrict__ out,
+                                               const OpTab<T> *__restrict__ tab,
+                                               const double *__restrict__ coef, T g, T mlam,
+                                               T *smem, T *__restrict__ outG, Acc<T> *acc) {
+  using S = EoShape<NQ>;
+  constexpr int H = S::H, NQ2 = S::NQ2, NP = S::NP, HP = NP / 2;
+  T *s_Ee = smem + S::EPB * 4 * NP, *s_Eo = s_Ee + H * H, *s_w = s_Eo + H * H;
+  __syncthreads();
+  for (int t = threadIdx.x; t < H * H; t += blockDim.x) {
+    s_Ee[t] = tab->Ee[t];
+    s_Eo[t] = tab->Eo[t];
+  }
+  for (int t = threadIdx.x; t < NQ; t += blockDim.x) s_w[t] = tab->w[t];
+  const int le = threadIdx.x / NQ2;
+  const int ij = threadIdx.x - le * NQ2;
+  const int i = ij % NQ, j = ij / NQ;
+  const int64_t slot = slot0 + le;
+  const bool active = le < S::EPB && slot < E;
+  const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  T *U = smem + (le < S::EPB ? le : 0) * 4 * NP;  // u, then the r outputs
+  T *Er = U + NP, *Es = U + 2 * NP, *AS = U + 3 * NP;
+  T ureg[NQ];
+  int32_t gid[FUSED ? NQ : 1];
+  if (active) {
+    const int64_t base = e * NP + ij;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      T v;
+      if (FUSED) {
+        const int32_t id = __ldcs(ids + base + k * NQ2);
+        gid[k] = id;
+        v = id != -1 ? in[id >= 0 ? id : -2 - id] : T(0);
+      } else if (GATHER_IN) {
+        const int32_t id = __ldcs(ids + base + k * NQ2);
+        v = id >= 0 ? in[id] : T(0);
+      } else {
+        v = __ldcs(in + base + k * NQ2);
+      }
+      ureg[k] = v;
+      U[ij + k * NQ2] = v;
+    }
+  }
+  __syncthreads();
+  // e/o values: threads i < h for the pair (i, N - i) of row j along r; the
+  // others for the pair (i - h, N - i + h) of column j along s
+  const bool rtask = i < H;
+  const int a = rtask ? i : i - H;
+  if (active) {
+    T *dst = rtask ? Er : Es;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const T u0 = rtask ? U[a + NQ * j + NQ2 * k] : U[j + NQ * a + NQ2 * k];
+      const T u1 = rtask ? U[(NQ - 1 - a) + NQ * j + NQ2 * k] : U[j + NQ * (NQ - 1 - a) + NQ2 * k];
+      dst[a + H * (j + NQ * k)] = u0 + u1;
+      dst[HP + a + H * (j + NQ * k)] = u0 - u1;
+    }
+  }
+  __syncthreads();
+  // one output pair per thread and layer: along r into U (u is dead), along s into AS
+  if (active) {
+    const T *src = rtask ? Er : Es;
+    T ee[H], eo[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      ee[m] = s_Ee[a * H + m];
+      eo[m] = s_Eo[a * H + m];
+    }
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      T se = T(0), so = T(0);
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        se = fmaT(ee[m], src[m + H * (j + NQ * k)], se);
+        so = fmaT(eo[m], src[HP + m + H * (j + NQ * k)], so);
+      }
+      if (rtask) {
+        U[a + NQ * j + NQ2 * k] = se + so;
+        U[(NQ - 1 - a) + NQ * j + NQ2 * k] = se - so;
+      } else {
+        AS[j + NQ * a + NQ2 * k] = se + so;
+        AS[j + NQ * (NQ - 1 - a) + NQ2 * k] = se - so;
+      }
+    }
+  }
+  // along t, from the thread's own column
+  T at[NQ];
+  if (active) {
+    T ev[H], ov[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      ev[m] = ureg[m] + ureg[NQ - 1 - m];
+      ov[m] = ureg[m] - ureg[NQ - 1 - m];
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      T se = T(0), so = T(0);
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        se = fmaT(s_Ee[k * H + m], ev[m], se);
+        so = fmaT(s_Eo[k * H + m], ov[m], so);
+      }
+      at[k] = se + so;
+      at[NQ - 1 - k] = se - so;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const T cg = (coef ? T(coef[e]) : T(1)) * g;
+  const T wij = s_w[i] * s_w[j];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const T sum = (U[ij + NQ2 * k] + AS[ij + NQ2 * k]) + at[k];
+    const T res = (wij * s_w[k]) * fmaT(cg, sum, mlam * ureg[k]);
+    if (FUSED) {
+      const int32_t id = gid[FUSED ? k : 0];
+      if (id >= 0) {
+        __stcs(out + e * NP + ij + k * NQ2, res);
+      } else if (id != -1) {
+        const T v = plus_zero(res);
+        __stcs(outG + (-2 - id), v);
+        acc->add(ureg[k], v);
+      }
+    } else {
+      __stcs(out + e * NP + ij + k * NQ2, res);
+    }
+  }
+}
+
+template <typename T, int NQ, bool GATHER_IN, bool FUSED>
+__global__ void __launch_bounds__(EoShape<NQ>::THREADS)
+    k_ax_local_eo(int64_t E, const int32_t *__restrict__ order,
+                  const int32_t *__restrict__ ids, const T *__restrict__ in,
+                  T *__restrict__ out, const OpTab<T> *__restrict__ tab,
+                  const double *__restrict__ coef, T g, T mlam, const CgState *st,
+                  T *__restrict__ outG, double *__restrict__ partials) {
+  using S = EoShape<NQ>;
+  __shared__ T smem[S::SMEM];
+  if (cg_halted(st)) return;
+  Acc<T> acc;
+  ax_elements_eo<T, NQ, GATHER_IN, FUSED>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out,
+                                          tab, coef, g, mlam, smem, outG, &acc);
+  if (FUSED && partials) {
+    const double part = block_sum<S::THREADS>(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = part;
+  }
+}
+
+// 1: the element kernels of A p use the even-odd form where it exists (the
+// default); 0: the direct sum factorisation everywhere.
+extern int g_op_evenodd;
+
 template <typename T, int NQ, bool GATHER_IN, bool FUSED>
 __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
     k_ax_local(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
@@ -164,9 +356,11 @@ __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
 // operator's partials hold one double per block).
 inline int64_t ax_blocks(int N, int64_t E) {
   switch (N + 1) {
-#define BS_AXB(NQ) \
-  case NQ:         \
-    return (E + OpShape<NQ>::EPB - 1) / OpShape<NQ>::EPB;
+#define BS_AXB(NQ)                                                      \
+  case NQ:                                                              \
+    return use_eo<NQ>() && g_op_evenodd                                 \
+               ? (E + EoShape<NQ>::EPB - 1) / EoShape<NQ>::EPB          \
+               : (E + OpShape<NQ>::EPB - 1) / OpShape<NQ>::EPB;
     BS_AXB(2) BS_AXB(3) BS_AXB(4) BS_AXB(5) BS_AXB(6) BS_AXB(7) BS_AXB(8) BS_AXB(9)
     BS_AXB(10) BS_AXB(11) BS_AXB(12) BS_AXB(13) BS_AXB(14) BS_AXB(15) BS_AXB(16)
 #undef BS_AXB
@@ -186,6 +380,15 @@ int launch_ax_local(int N, int64_t E, const int32_t *order, const int32_t *ids, 
   if (E == 0) return BS_OK;
 #define BS_AX_CASE(NQ)                                                                   \
   case NQ: {                                                                             \
+    if constexpr (use_eo<NQ>()) {                                                        \
+      if (g_op_evenodd) {                                                                \
+        using Se = EoShape<NQ>;                                                          \
+        const int64_t grid = (E + Se::EPB - 1) / Se::EPB;                                \
+        k_ax_local_eo<T, NQ, GATHER_IN, FUSED><<<(unsigned)grid, Se::THREADS, 0, s>>>(   \
+            E, order, ids, in, out, tab, coef, g, mlam, st, outG, partials);             \
+        break;                                                                           \
+      }                                                                                  \
+    }                                                                                    \
     using Sh = OpShape<NQ>;                                                              \
     const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                    \
     k_ax_local<T, NQ, GATHER_IN, FUSED><<<(unsigned)grid, Sh::THREADS, 0, s>>>(          \

@@ -1,5 +1,7 @@
-"""The fused operator (bs_operator_fusion): single-copy nodes written by the
-element kernel, shared ones gathered from their own CSR.
+"""Operator modes (bs_operator_mode).
+
+The fused operator (BS_OP_FUSED): single-copy nodes written by the element
+kernel, shared ones gathered from their own CSR.
 
 A p must be bitwise that of the unfused path -- element kernel plus the
 gather of every row -- because a one-copy row's serial sum is +0 + v, which
@@ -8,6 +10,11 @@ FP32 (inside the refined solver) element kernels, on natural-boundary,
 Dirichlet-masked, randomly masked maps and maps with global nodes no local
 node references.  CG with the fused p.Ap (summed in another order) follows
 the unfused CG to rounding and meets the oracle's residual.
+
+The even-odd element kernels (the default for odd N <= 9) against the direct
+sum factorisation (BS_OP_DIRECT) and the oracle: the same 1e-12 max|A p|
+bound as the direct kernel (both round every term once; the even-odd form
+adds the e/o sums and its tables' rounding, a few units of eps sum |K||u|).
 """
 import numpy as np
 import pytest
@@ -21,9 +28,9 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture
 def fusion():
-    prev = bs.operator_fusion(-1)
+    prev = bs.operator_mode(-1)
     yield
-    bs.operator_fusion(prev)
+    bs.operator_mode(prev)
 
 
 def cuda(a):
@@ -40,7 +47,8 @@ def both(fn):
 
 
 def test_fusion_switch(fusion):
-    assert bs.operator_fusion(-1) == 0  # the default
+    assert bs.operator_mode(-1) == 0  # the default: unfused, even-odd
+    assert bs.operator_fusion(-1) == 0
     assert bs.operator_fusion(1) == 0
     assert bs.operator_fusion(-1) == 1
     assert bs.operator_fusion(0) == 1
@@ -133,3 +141,42 @@ def test_fused_small_config_histories_match_oracle(fusion):
     np.testing.assert_allclose(h[:, 0], ha, rtol=1e-10)
     np.testing.assert_allclose(h[:, 1], hb, rtol=1e-10)
     np.testing.assert_allclose(h[:, 2], hr[1:], rtol=1e-10)
+
+
+@pytest.mark.parametrize("K,N", [(5, 1), (4, 3), (3, 5), (3, 7), (2, 9)])
+@pytest.mark.parametrize("fused", [0, bs.BS_OP_FUSED])
+def test_evenodd_matches_direct_and_oracle(fusion, K, N, fused):
+    m = synth.Mesh(K, N, seed=K + 2 * N)
+    coef = synth.lognormal(m.E, 6)
+    Z = bs.Map(m.E, N, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, 0.7, coef)
+    p = cuda(synth.uniform(m.NG, 5))
+    uL = cuda(synth.uniform(m.NL, 6))
+    bs.operator_mode(fused)
+    a, aL = P.apply_A(p).clone(), P.apply_local(uL).clone()
+    bs.operator_mode(fused | bs.BS_OP_DIRECT)
+    d, dL = P.apply_A(p).clone(), P.apply_local(uL).clone()
+    want = oracle.apply_A(m.E, N, m.h, 0.7, m.ids, m.NG, p.cpu().numpy(), coef)
+    wantL = oracle.apply_local(m.E, N, m.h, 0.7, uL.cpu().numpy(), coef)
+    for got in (a, d):
+        assert np.abs(got.cpu().numpy() - want).max() <= 1e-12 * np.abs(want).max()
+    for got in (aL, dL):
+        assert np.abs(got.cpu().numpy() - wantL).max() <= 1e-12 * np.abs(wantL).max()
+    assert not torch.equal(a, d) or N == 1  # the even-odd kernel did run
+
+
+def test_evenodd_fp32_refined_and_scattered(fusion):
+    """The FP32 even-odd kernel inside the refined solver, and the even-odd
+    kernel on contiguous local data in scattered-storage CG."""
+    m = synth.Mesh(4, 7, seed=2)
+    Z = bs.Map(m.E, 7, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, 1.0)
+    bh = synth.uniform(m.NG, 3)
+    b = cuda(bh)
+    for flags in (0, bs.BS_CG_SCATTERED):
+        x, info = P.cg(b, tol=1e-10, maxit=3000, flags=flags)
+        r = bh - oracle.apply_A(m.E, 7, m.h, 1.0, m.ids, m.NG, x.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(bh)
+    x, info = P.cg_refined_f32(b, tol=1e-10)
+    r = bh - oracle.apply_A(m.E, 7, m.h, 1.0, m.ids, m.NG, x.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(bh)
