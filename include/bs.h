@@ -192,12 +192,12 @@ int bs_apply_A_ff(const bs_problem *prob, const double *p, double *Ap, void *str
  *   differs only by summation order.  Measured slower on GB300
  *   (partial-sector writes into Ap; N = 7 on 48^3: 1.37 vs 1.24 ms per
  *   float-float A p).
- *  BS_OP_DIRECT: the FP64 and FP32 element kernels contract with the full
- *   1-D stiffness K = D^T W D (3 (N+1) fused multiply-adds per node).
- *   Without it, for odd N <= 9, they use the even-odd form of the
+ *  BS_OP_DIRECT: the element kernels (FP64, FP32, float-float) contract
+ *   with the full 1-D stiffness K = D^T W D (3 (N+1) multiply-adds per
+ *   node).  Without it, for odd N <= 9, they use the even-odd form of the
  *   centrosymmetric W^-1 K (Solomonoff's decomposition; half-length
- *   contractions, about a quarter fewer FP64 operations per node); results
- *   differ by rounding only.  The float-float kernel is always direct.
+ *   contractions, about a quarter fewer operations per node); results
+ *   differ by rounding only.
  * Returns the previous mode; a negative value only queries it.  Not
  * thread-safe against solves in flight. */
 enum { BS_OP_FUSED = 1, BS_OP_DIRECT = 2 };

@@ -186,6 +186,8 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
         tab.Eo[a * hq + m] = o;
         tabf.Ee[a * hq + m] = (float)e;
         tabf.Eo[a * hq + m] = (float)o;
+        split(e, tabff.Eeh[a * hq + m], tabff.Eel[a * hq + m]);
+        split(o, tabff.Eoh[a * hq + m], tabff.Eol[a * hq + m]);
       }
   }
   for (int i = 0; i < Nq; ++i) {

@@ -328,8 +328,8 @@ __global__ void __launch_bounds__(EoShape<NQ>::THREADS)
   }
 }
 
-// 1: the element kernels of A p use the even-odd form where it exists (the
-// default); 0: the direct sum factorisation everywhere.
+// 1: the element kernels of A p (FP64, FP32, float-float) use the even-odd
+// form where it exists (the default); 0: the direct sum factorisation.
 extern int g_op_evenodd;
 
 template <typename T, int NQ, bool GATHER_IN, bool FUSED>

@@ -37,6 +37,9 @@ struct OpTabFF {
   float Kh[kMaxNq * kMaxNq], Kl[kMaxNq * kMaxNq];
   float Wh[kMaxNq * kMaxNq], Wl[kMaxNq * kMaxNq];
   float wh[kMaxNq], wl[kMaxNq];
+  // the even-odd halves OpTab::Ee, OpTab::Eo as float pairs
+  float Eeh[(kMaxNq / 2) * (kMaxNq / 2)], Eel[(kMaxNq / 2) * (kMaxNq / 2)];
+  float Eoh[(kMaxNq / 2) * (kMaxNq / 2)], Eol[(kMaxNq / 2) * (kMaxNq / 2)];
 };
 
 // x = h + l exactly up to 2^-48 |x| (see the header comment); integer and
@@ -209,6 +212,205 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
   }
 }
 
+// a + b for unevaluated float pairs: TwoSum of the high parts, low parts
+// and the rounding error added (not renormalised, as in ff_fma).
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  return FF{s, (a.lo + b.lo) + err};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+
+// The even-odd form of bs_op.cuh (ax_elements_eo) in float-float arithmetic:
+// the same phases, every value a float pair (e/o values by ff_add, the
+// half-length contractions by ff_fma), result W3 (c (h/2) sum + lambda
+// (h/2)^3 u) joined into a double.  smem holds EoShape<NQ>::SMEM_FF floats.
+template <int NQ>
+struct EoShapeFF {
+  static constexpr int SMEM = EoShape<NQ>::EPB * 8 * EoShape<NQ>::NP +
+                              4 * EoShape<NQ>::H * EoShape<NQ>::H + 2 * NQ;
+};
+
+template <int NQ, bool GATHER_IN, bool FUSED>
+__device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
+                                                  const int32_t *__restrict__ order,
+                                                  const int32_t *__restrict__ ids,
+                                                  const double *__restrict__ in,
+                                                  double *__restrict__ out,
+                                                  const OpTabFF *__restrict__ tab,
+                                                  const double *__restrict__ coef, double g,
+                                                  double mlam, float *smem,
+                                                  double *__restrict__ outG,
+                                                  Acc<double> *acc) {
+  using S = EoShape<NQ>;
+  constexpr int H = S::H, NQ2 = S::NQ2, NP = S::NP, HP = NP / 2, HH = H * H;
+  float *s_t = smem + S::EPB * 8 * NP;  // Eeh, Eel, Eoh, Eol, wh, wl
+  __syncthreads();
+  for (int t = threadIdx.x; t < HH; t += blockDim.x) {
+    s_t[t] = tab->Eeh[t];
+    s_t[HH + t] = tab->Eel[t];
+    s_t[2 * HH + t] = tab->Eoh[t];
+    s_t[3 * HH + t] = tab->Eol[t];
+  }
+  for (int t = threadIdx.x; t < NQ; t += blockDim.x) {
+    s_t[4 * HH + t] = tab->wh[t];
+    s_t[4 * HH + NQ + t] = tab->wl[t];
+  }
+  const float *s_w = s_t + 4 * HH;
+  const int le = threadIdx.x / NQ2;
+  const int ij = threadIdx.x - le * NQ2;
+  const int i = ij % NQ, j = ij / NQ;
+  const int64_t slot = slot0 + le;
+  const bool active = le < S::EPB && slot < E;
+  const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  float *Uh = smem + (le < S::EPB ? le : 0) * 8 * NP, *Ul = Uh + NP;  // u, then r outputs
+  float *Erh = Uh + 2 * NP, *Erl = Uh + 3 * NP, *Esh = Uh + 4 * NP, *Esl = Uh + 5 * NP;
+  float *ASh = Uh + 6 * NP, *ASl = Uh + 7 * NP;
+  float rh[NQ], rl[NQ];
+  int32_t gid[FUSED ? NQ : 1];
+  if (active) {
+    const int64_t base = e * NP + ij;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      double v;
+      if (FUSED) {
+        const int32_t id = __ldcs(ids + base + k * NQ2);
+        gid[k] = id;
+        v = id != -1 ? in[id >= 0 ? id : -2 - id] : 0.0;
+      } else if (GATHER_IN) {
+        const int32_t id = __ldcs(ids + base + k * NQ2);
+        v = id >= 0 ? in[id] : 0.0;
+      } else {
+        v = __ldcs(in + base + k * NQ2);
+      }
+      const FF f = ff_split(v);
+      rh[k] = f.hi;
+      rl[k] = f.lo;
+      Uh[ij + k * NQ2] = f.hi;
+      Ul[ij + k * NQ2] = f.lo;
+    }
+  }
+  __syncthreads();
+  const bool rtask = i < H;
+  const int a = rtask ? i : i - H;
+  if (active) {
+    float *dh = rtask ? Erh : Esh, *dl = rtask ? Erl : Esl;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const int l0 = rtask ? a + NQ * j + NQ2 * k : j + NQ * a + NQ2 * k;
+      const int l1 = rtask ? (NQ - 1 - a) + NQ * j + NQ2 * k : j + NQ * (NQ - 1 - a) + NQ2 * k;
+      const FF u0{Uh[l0], Ul[l0]}, u1{Uh[l1], Ul[l1]};
+      const FF ev = ff_add(u0, u1), ov = ff_add(u0, ff_neg(u1));
+      const int d = a + H * (j + NQ * k);
+      dh[d] = ev.hi;
+      dl[d] = ev.lo;
+      dh[HP + d] = ov.hi;
+      dl[HP + d] = ov.lo;
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const float *sh = rtask ? Erh : Esh, *sl = rtask ? Erl : Esl;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      FF se{0.f, 0.f}, so{0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const int d = m + H * (j + NQ * k);
+        ff_fma(se, s_t[a * H + m], s_t[HH + a * H + m], sh[d], sl[d]);
+        ff_fma(so, s_t[2 * HH + a * H + m], s_t[3 * HH + a * H + m], sh[HP + d], sl[HP + d]);
+      }
+      const FF p = ff_add(se, so), q = ff_add(se, ff_neg(so));
+      if (rtask) {
+        const int l0 = a + NQ * j + NQ2 * k, l1 = (NQ - 1 - a) + NQ * j + NQ2 * k;
+        Uh[l0] = p.hi;
+        Ul[l0] = p.lo;
+        Uh[l1] = q.hi;
+        Ul[l1] = q.lo;
+      } else {
+        const int l0 = j + NQ * a + NQ2 * k, l1 = j + NQ * (NQ - 1 - a) + NQ2 * k;
+        ASh[l0] = p.hi;
+        ASl[l0] = p.lo;
+        ASh[l1] = q.hi;
+        ASl[l1] = q.lo;
+      }
+    }
+  }
+  FF at[NQ];
+  if (active) {
+    FF ev[H], ov[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      const FF u0{rh[m], rl[m]}, u1{rh[NQ - 1 - m], rl[NQ - 1 - m]};
+      ev[m] = ff_add(u0, u1);
+      ov[m] = ff_add(u0, ff_neg(u1));
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      FF se{0.f, 0.f}, so{0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        ff_fma(se, s_t[k * H + m], s_t[HH + k * H + m], ev[m].hi, ev[m].lo);
+        ff_fma(so, s_t[2 * HH + k * H + m], s_t[3 * HH + k * H + m], ov[m].hi, ov[m].lo);
+      }
+      at[k] = ff_add(se, so);
+      at[NQ - 1 - k] = ff_add(se, ff_neg(so));
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const FF cg = ff_split((coef ? coef[e] : 1.0) * g);
+  const FF ml = ff_split(mlam);
+  FF wij{0.f, 0.f};
+  ff_fma(wij, s_w[i], s_w[NQ + i], s_w[j], s_w[NQ + j]);
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const int l = ij + NQ2 * k;
+    const FF sum = ff_add(ff_add(FF{Uh[l], Ul[l]}, FF{ASh[l], ASl[l]}), at[k]);
+    FF o{0.f, 0.f};
+    ff_fma(o, cg.hi, cg.lo, sum.hi, sum.lo);
+    ff_fma(o, ml.hi, ml.lo, rh[k], rl[k]);
+    FF w3{0.f, 0.f};
+    ff_fma(w3, wij.hi, wij.lo, s_w[k], s_w[NQ + k]);
+    FF r{0.f, 0.f};
+    ff_fma(r, w3.hi, w3.lo, o.hi, o.lo);
+    const double res = ff_widen(r.hi) + ff_widen(r.lo);
+    if (FUSED) {
+      const int32_t id = gid[FUSED ? k : 0];
+      if (id >= 0) {
+        __stcs(out + e * NP + l, res);
+      } else if (id != -1) {
+        const double v = plus_zero(res);
+        __stcs(outG + (-2 - id), v);
+        acc->add(__ldg(in + (-2 - id)), v);
+      }
+    } else {
+      __stcs(out + e * NP + l, res);
+    }
+  }
+}
+
+template <int NQ, bool GATHER_IN, bool FUSED>
+__global__ void __launch_bounds__(EoShape<NQ>::THREADS)
+    k_ax_local_ff_eo(int64_t E, const int32_t *__restrict__ order,
+                     const int32_t *__restrict__ ids, const double *__restrict__ in,
+                     double *__restrict__ out, const OpTabFF *__restrict__ tab,
+                     const double *__restrict__ coef, double g, double mlam,
+                     const CgState *st, double *__restrict__ outG,
+                     double *__restrict__ partials) {
+  using S = EoShape<NQ>;
+  __shared__ float smem[EoShapeFF<NQ>::SMEM];
+  if (cg_halted(st)) return;
+  Acc<double> acc;
+  ax_elements_ff_eo<NQ, GATHER_IN, FUSED>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out,
+                                          tab, coef, g, mlam, smem, outG, &acc);
+  if (FUSED && partials) {
+    const double part = block_sum<S::THREADS>(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = part;
+  }
+}
+
 template <int NQ, bool GATHER_IN, bool FUSED>
 __global__ void __launch_bounds__(OpShape<NQ>::THREADS)
     k_ax_local_ff(int64_t E, const int32_t *__restrict__ order, const int32_t *__restrict__ ids,
@@ -239,6 +441,15 @@ int launch_ax_local_ff(int N, int64_t E, const int32_t *order, const int32_t *id
   if (E == 0) return BS_OK;
 #define BS_AXFF_CASE(NQ)                                                              \
   case NQ: {                                                                          \
+    if constexpr (use_eo<NQ>()) {                                                     \
+      if (g_op_evenodd) {                                                             \
+        using Se = EoShape<NQ>;                                                       \
+        const int64_t grid = (E + Se::EPB - 1) / Se::EPB;                             \
+        k_ax_local_ff_eo<NQ, GATHER_IN, FUSED><<<(unsigned)grid, Se::THREADS, 0, s>>>( \
+            E, order, ids, in, out, tab, coef, g, mlam, st, outG, partials);          \
+        break;                                                                        \
+      }                                                                               \
+    }                                                                                 \
     using Sh = OpShape<NQ>;                                                           \
     const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                 \
     k_ax_local_ff<NQ, GATHER_IN, FUSED><<<(unsigned)grid, Sh::THREADS, 0, s>>>(       \

@@ -24,9 +24,20 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+@pytest.fixture
+def mode():
+    prev = bs.operator_mode(-1)
+    yield bs.operator_mode
+    bs.operator_mode(prev)
+
+
 @pytest.mark.parametrize("K,N", [(2, 1), (2, 2), (2, 3), (2, 5), (1, 7), (1, 9)])
 @pytest.mark.parametrize("with_coef", [False, True])
-def test_apply_A_ff_within_bound(K, N, with_coef):
+@pytest.mark.parametrize("direct", [False, True])
+def test_apply_A_ff_within_bound(mode, K, N, with_coef, direct):
+    """Both element-kernel forms (even-odd for odd N, the default, and
+    direct) of both operators stay within the bound."""
+    mode(bs.BS_OP_DIRECT if direct else 0)
     m = synth.Mesh(K, N, seed=3)
     lam = 1e-2
     coef = synth.lognormal(m.E, 5) if with_coef else None
