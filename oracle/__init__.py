@@ -73,6 +73,13 @@ _SIGS = {
     "bso_cg": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int, _int,
                       _D, _D, _D]),
     "bso_pcg_jacobi": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int, _D]),
+    "bso_apply_A_geo": (_int, [_int, _int, _dbl, _D, _D, _I, _i64, _D, _D]),
+    "bso_apply_local_geo": (_int, [_int, _int, _dbl, _D, _D, _D, _D]),
+    "bso_diag_A_geo": (_int, [_int, _int, _dbl, _D, _D, _I, _i64, _D]),
+    "bso_cg_geo": (_int, [_int, _int, _dbl, _D, _D, _I, _i64, _D, _D, _dbl, _int, _int,
+                          _D, _D, _D]),
+    "bso_pcg_jacobi_geo": (_int, [_int, _int, _dbl, _D, _D, _I, _i64, _D, _D, _dbl, _int,
+                                  _D]),
     "bso_cg_ir_f32": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int,
                              _dbl, _int, ctypes.POINTER(_int), _D]),
 }
@@ -296,6 +303,70 @@ def pcg_jacobi(E, N, h, lam, ids, NG, b, tol=1e-8, maxit=1000, coef=None):
                               _d(x), float(tol), int(maxit), _d(hr))
     if it < 0:
         raise RuntimeError(f"bso_pcg_jacobi failed ({it})")
+    return x, it, hr[:it + 1]
+
+
+# ---------------------------------------------------------------- general hexahedra
+# verts: float64 [E, 8, 3], corner v = vx + 2 (vy + 2 vz) of element e (the
+# trilinear map of bs_oracle.c); the operator is the same weak form with the
+# non-affine geometric factors w det J J^-1 J^-T at every GLL node.
+
+def _verts(verts, E):
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    if v.size != 24 * E:
+        raise ValueError("verts must hold 8 corners x 3 coordinates per element")
+    return v
+
+
+def apply_A_geo(E, N, lam, verts, ids, NG, p, coef=None):
+    ids, p, coef, v = _ids(ids), _f64(p), _coef(coef), _verts(verts, E)
+    Ap = np.empty(int(NG))
+    rc = lib().bso_apply_A_geo(E, N, float(lam), _d(coef), _d(v), _i(ids), int(NG), _d(p),
+                               _d(Ap))
+    if rc:
+        raise RuntimeError(f"bso_apply_A_geo failed ({rc})")
+    return Ap
+
+
+def apply_local_geo(E, N, lam, verts, uL, coef=None):
+    uL, coef, v = _f64(uL), _coef(coef), _verts(verts, E)
+    out = np.empty_like(uL)
+    rc = lib().bso_apply_local_geo(E, N, float(lam), _d(coef), _d(v), _d(uL), _d(out))
+    if rc:
+        raise RuntimeError(f"bso_apply_local_geo failed ({rc})")
+    return out
+
+
+def diag_A_geo(E, N, lam, verts, ids, NG, coef=None):
+    ids, coef, v = _ids(ids), _coef(coef), _verts(verts, E)
+    d = np.empty(int(NG))
+    rc = lib().bso_diag_A_geo(E, N, float(lam), _d(coef), _d(v), _i(ids), int(NG), _d(d))
+    if rc:
+        raise RuntimeError(f"bso_diag_A_geo failed ({rc})")
+    return d
+
+
+def cg_geo(E, N, lam, verts, ids, NG, b, tol=1e-8, maxit=1000, fixed_iters=False, coef=None):
+    """Algorithm 1 on the general-hexahedron operator.  (x, iters, alpha, beta, rr)."""
+    ids, b, coef, v = _ids(ids), _f64(b), _coef(coef), _verts(verts, E)
+    x = np.zeros(int(NG))
+    ha, hb, hr = np.zeros(maxit + 1), np.zeros(maxit + 1), np.zeros(maxit + 2)
+    it = lib().bso_cg_geo(E, N, float(lam), _d(coef), _d(v), _i(ids), int(NG), _d(b), _d(x),
+                          float(tol), int(maxit), int(bool(fixed_iters)), _d(ha), _d(hb),
+                          _d(hr))
+    if it < 0:
+        raise RuntimeError(f"bso_cg_geo failed ({it})")
+    return x, it, ha[:it], hb[:it], hr[:it + 1]
+
+
+def pcg_jacobi_geo(E, N, lam, verts, ids, NG, b, tol=1e-8, maxit=1000, coef=None):
+    ids, b, coef, v = _ids(ids), _f64(b), _coef(coef), _verts(verts, E)
+    x = np.zeros(int(NG))
+    hr = np.zeros(maxit + 2)
+    it = lib().bso_pcg_jacobi_geo(E, N, float(lam), _d(coef), _d(v), _i(ids), int(NG), _d(b),
+                                  _d(x), float(tol), int(maxit), _d(hr))
+    if it < 0:
+        raise RuntimeError(f"bso_pcg_jacobi_geo failed ({it})")
     return x, it, hr[:it + 1]
 
 

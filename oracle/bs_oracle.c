@@ -23,7 +23,10 @@
  *    starting from +0.0; a global node with no copies is 0  (eq. scatter_def)
  *  - BS7 leaves masked (id < 0) local entries untouched      (Sec. 5)
  *  - the operator is the affine-cube GLL spectral element discretisation of
- *    the Helmholtz weak form with collocated (lumped) quadrature (Sec. 2)
+ *    the Helmholtz weak form with collocated (lumped) quadrature (Sec. 2);
+ *    the *_geo entry points take general trilinear hexahedra instead
+ *    (eight corner vertices per element; the non-affine geometric factors
+ *    that the paper's BS6/BS7 discussion mentions, Sec. 5)
  *  - CG stops when r.r <= tol^2 * (b.b)                       (Algorithm 1)
  */
 #include <math.h>
@@ -214,12 +217,109 @@ typedef struct {
   const double *coef; /* per-element stiffness coefficient or NULL */
   const int32_t *ids; /* local -> global, length E*(N+1)^3, < 0 masked */
   int64_t NG;
+  const double *verts; /* NULL: affine cubes of side h; else 24 per element */
 } bso_problem;
+
+/* ------------------------------------------------------------------------ */
+/* General hexahedra.  Element e is the trilinear image of [-1,1]^3 with    */
+/* corner v = vx + 2 (vy + 2 vz) (vx, vy, vz in {0, 1}) at                 */
+/* verts[24 e + 3 v + d], d = x, y, z:                                      */
+/*   x(r,s,t) = sum_v X_v (1 + sx r)(1 + sy s)(1 + sz t) / 8,  sx = 2vx - 1. */
+/* With J = dx/dr (J[d][p] = d x_d / d r_p) at a GLL node q,                */
+/*   (A_e u)_n = c_e sum_q w_q det J  (J^-T grad_r l_n)(q) . (J^-T grad_r u)(q) */
+/*             + lambda w_n det J(n) u_n,                                   */
+/* i.e. the reference gradient contracted with G = w_q det J J^-1 J^-T.     */
+/* ------------------------------------------------------------------------ */
+
+static void jacobian(const double *X, double r, double s, double t, double J[3][3]) {
+  for (int d = 0; d < 3; ++d) J[d][0] = J[d][1] = J[d][2] = 0.0;
+  for (int v = 0; v < 8; ++v) {
+    const double sx = (v & 1) ? 1.0 : -1.0, sy = (v & 2) ? 1.0 : -1.0, sz = (v & 4) ? 1.0 : -1.0;
+    const double dr = sx * (1.0 + sy * s) * (1.0 + sz * t) / 8.0;
+    const double ds = (1.0 + sx * r) * sy * (1.0 + sz * t) / 8.0;
+    const double dt = (1.0 + sx * r) * (1.0 + sy * s) * sz / 8.0;
+    for (int d = 0; d < 3; ++d) {
+      J[d][0] += X[3 * v + d] * dr;
+      J[d][1] += X[3 * v + d] * ds;
+      J[d][2] += X[3 * v + d] * dt;
+    }
+  }
+}
+
+static double det3(double J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+/* G[p][q] = wq det J sum_d Jinv[p][d] Jinv[q][d], Jinv = J^-1 by cofactors. */
+static double metric(double J[3][3], double wq, double G[3][3]) {
+  const double det = det3(J);
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) {
+      double v = 0.0;
+      for (int d = 0; d < 3; ++d) v += inv[p][d] * inv[q][d];
+      G[p][q] = wq * det * v;
+    }
+  return det;
+}
+
+static void element_apply_geo(const bso_problem *P, const double *r, const double *w,
+                              const double *D, int e, const double *u, double *Au,
+                              double *ur, double *us, double *ut) {
+  const int N = P->N, Nq = N + 1;
+  const double ce = P->coef ? P->coef[e] : 1.0;
+  const double *X = P->verts + (int64_t)e * 24;
+  double J[3][3], G[3][3];
+#define IDX(i, j, k) ((i) + Nq * ((j) + Nq * (k)))
+  for (int c = 0; c < Nq; ++c)
+    for (int b = 0; b < Nq; ++b)
+      for (int a = 0; a < Nq; ++a) {
+        double dr = 0.0, ds = 0.0, dt = 0.0;
+        for (int n = 0; n < Nq; ++n) {
+          dr = fma(D[a * Nq + n], u[IDX(n, b, c)], dr);
+          ds = fma(D[b * Nq + n], u[IDX(a, n, c)], ds);
+          dt = fma(D[c * Nq + n], u[IDX(a, b, n)], dt);
+        }
+        jacobian(X, r[a], r[b], r[c], J);
+        metric(J, w[a] * w[b] * w[c], G);
+        ur[IDX(a, b, c)] = G[0][0] * dr + G[0][1] * ds + G[0][2] * dt;
+        us[IDX(a, b, c)] = G[1][0] * dr + G[1][1] * ds + G[1][2] * dt;
+        ut[IDX(a, b, c)] = G[2][0] * dr + G[2][1] * ds + G[2][2] * dt;
+      }
+  for (int k = 0; k < Nq; ++k)
+    for (int j = 0; j < Nq; ++j)
+      for (int i = 0; i < Nq; ++i) {
+        double s = 0.0;
+        for (int n = 0; n < Nq; ++n) {
+          s = fma(D[n * Nq + i], ur[IDX(n, j, k)], s);
+          s = fma(D[n * Nq + j], us[IDX(i, n, k)], s);
+          s = fma(D[n * Nq + k], ut[IDX(i, j, n)], s);
+        }
+        jacobian(X, r[i], r[j], r[k], J);
+        const double mass = (w[i] * w[j] * w[k]) * det3(J) * u[IDX(i, j, k)];
+        Au[IDX(i, j, k)] = fma(ce, s, P->lambda * mass);
+      }
+#undef IDX
+}
 
 static void element_apply(const bso_problem *P, const double *r, const double *w,
                           const double *D, int e, const double *u, double *Au,
                           double *ur, double *us, double *ut) {
-  (void)r;
+  if (P->verts) {
+    element_apply_geo(P, r, w, D, e, u, Au, ur, us, ut);
+    return;
+  }
   const int N = P->N, Nq = N + 1;
   const double ce = P->coef ? P->coef[e] : 1.0;
   const double g = 0.5 * P->h;          /* (h/2): stiffness geometric factor */
@@ -329,6 +429,53 @@ int bso_diag_A(int E, int N, double h, double lambda, const double *coef,
   return 0;
 }
 
+/* The general-hexahedron operator (see jacobian above). */
+int bso_apply_A_geo(int E, int N, double lambda, const double *coef, const double *verts,
+                    const int32_t *ids, int64_t NG, const double *p, double *Ap) {
+  bso_problem P = {E, N, 1.0, lambda, coef, ids, NG, verts};
+  return apply_A(&P, p, Ap);
+}
+
+int bso_apply_local_geo(int E, int N, double lambda, const double *coef, const double *verts,
+                        const double *uL, double *AuL) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  double r[33], w[33], D[33 * 33];
+  if (bso_gll(N, r, w, D)) return 1;
+  bso_problem P = {E, N, 1.0, lambda, coef, NULL, 0, verts};
+  double *tmp = malloc(sizeof(double) * 3 * Np);
+  if (!tmp) return 2;
+  for (int e = 0; e < E; ++e)
+    element_apply(&P, r, w, D, e, uL + (int64_t)e * Np, AuL + (int64_t)e * Np, tmp,
+                  tmp + Np, tmp + 2 * Np);
+  free(tmp);
+  return 0;
+}
+
+/* diag(A) = Z^T diag(A_L), each diagonal entry of A_e read off A_e applied
+ * to the unit vector of its node. */
+int bso_diag_A_geo(int E, int N, double lambda, const double *coef, const double *verts,
+                   const int32_t *ids, int64_t NG, double *diag) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  double r[33], w[33], D[33 * 33];
+  if (bso_gll(N, r, w, D)) return 1;
+  bso_problem P = {E, N, 1.0, lambda, coef, ids, NG, verts};
+  double *buf = malloc(sizeof(double) * 5 * Np);
+  if (!buf) return 2;
+  double *unit = buf, *col = buf + Np;
+  for (int64_t gI = 0; gI < NG; ++gI) diag[gI] = 0.0;
+  for (int e = 0; e < E; ++e)
+    for (int l = 0; l < Np; ++l) {
+      const int32_t id = ids[(int64_t)e * Np + l];
+      if (id < 0) continue;
+      for (int m = 0; m < Np; ++m) unit[m] = 0.0;
+      unit[l] = 1.0;
+      element_apply(&P, r, w, D, e, unit, col, col + Np, col + 2 * Np, col + 3 * Np);
+      diag[id] = diag[id] + col[l];
+    }
+  free(buf);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Training pairs of the learned element preconditioner (no counterpart in  */
 /* the paper; the definition this project chose).  For a global residual r  */
@@ -428,11 +575,10 @@ int bso_interior_pairs(int E, int N, double h, double lambda, const double *coef
 /* Returns the iteration count, or -1 on a breakdown (p.Ap <= 0 or not      */
 /* finite), -2 on an allocation failure.                                    */
 /* ------------------------------------------------------------------------ */
-int bso_cg(int E, int N, double h, double lambda, const double *coef,
-           const int32_t *ids, int64_t NG, const double *b, double *x, double tol,
-           int maxit, int fixed_iters, double *hist_alpha, double *hist_beta,
-           double *hist_rr) {
-  bso_problem P = {E, N, h, lambda, coef, ids, NG};
+static int cg_run(const bso_problem *Pp, const double *b, double *x, double tol, int maxit,
+                  int fixed_iters, double *hist_alpha, double *hist_beta, double *hist_rr) {
+  const bso_problem P = *Pp;
+  const int64_t NG = P.NG;
   double *r = malloc(sizeof(double) * 3 * NG);
   if (!r) return -2;
   double *p = r + NG, *Ap = p + NG;
@@ -463,17 +609,36 @@ int bso_cg(int E, int N, double h, double lambda, const double *coef,
   return j;
 }
 
+int bso_cg(int E, int N, double h, double lambda, const double *coef,
+           const int32_t *ids, int64_t NG, const double *b, double *x, double tol,
+           int maxit, int fixed_iters, double *hist_alpha, double *hist_beta,
+           double *hist_rr) {
+  bso_problem P = {E, N, h, lambda, coef, ids, NG, NULL};
+  return cg_run(&P, b, x, tol, maxit, fixed_iters, hist_alpha, hist_beta, hist_rr);
+}
+
+int bso_cg_geo(int E, int N, double lambda, const double *coef, const double *verts,
+               const int32_t *ids, int64_t NG, const double *b, double *x, double tol,
+               int maxit, int fixed_iters, double *hist_alpha, double *hist_beta,
+               double *hist_rr) {
+  bso_problem P = {E, N, 1.0, lambda, coef, ids, NG, verts};
+  return cg_run(&P, b, x, tol, maxit, fixed_iters, hist_alpha, hist_beta, hist_rr);
+}
+
 /* Jacobi-preconditioned CG: Algorithm 1 with z = diag(A)^{-1} r, alpha =
  * r.z / p.Ap, beta = r_{j+1}.z_{j+1} / r_j.z_j, p = z + beta p.  Stops on the
  * unpreconditioned r.r <= tol^2 (b.b). */
-int bso_pcg_jacobi(int E, int N, double h, double lambda, const double *coef,
-                   const int32_t *ids, int64_t NG, const double *b, double *x,
-                   double tol, int maxit, double *hist_rr) {
-  bso_problem P = {E, N, h, lambda, coef, ids, NG};
+static int pcg_run(const bso_problem *Pp, const double *b, double *x, double tol, int maxit,
+                   double *hist_rr) {
+  const bso_problem P = *Pp;
+  const int64_t NG = P.NG;
   double *r = malloc(sizeof(double) * 5 * NG);
   if (!r) return -2;
   double *p = r + NG, *Ap = p + NG, *z = Ap + NG, *dg = z + NG;
-  bso_diag_A(E, N, h, lambda, coef, ids, NG, dg);
+  if (P.verts)
+    bso_diag_A_geo(P.E, P.N, P.lambda, P.coef, P.verts, P.ids, NG, dg);
+  else
+    bso_diag_A(P.E, P.N, P.h, P.lambda, P.coef, P.ids, NG, dg);
   apply_A(&P, x, Ap);
   for (int64_t i = 0; i < NG; ++i) r[i] = b[i] - Ap[i];
   for (int64_t i = 0; i < NG; ++i) z[i] = r[i] / dg[i];
@@ -498,6 +663,20 @@ int bso_pcg_jacobi(int E, int N, double h, double lambda, const double *coef,
   }
   free(r);
   return j;
+}
+
+int bso_pcg_jacobi(int E, int N, double h, double lambda, const double *coef,
+                   const int32_t *ids, int64_t NG, const double *b, double *x,
+                   double tol, int maxit, double *hist_rr) {
+  bso_problem P = {E, N, h, lambda, coef, ids, NG, NULL};
+  return pcg_run(&P, b, x, tol, maxit, hist_rr);
+}
+
+int bso_pcg_jacobi_geo(int E, int N, double lambda, const double *coef, const double *verts,
+                       const int32_t *ids, int64_t NG, const double *b, double *x,
+                       double tol, int maxit, double *hist_rr) {
+  bso_problem P = {E, N, 1.0, lambda, coef, ids, NG, verts};
+  return pcg_run(&P, b, x, tol, maxit, hist_rr);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -95,11 +95,15 @@ class Mesh:
     global node).  dirichlet=True masks every local copy of a node on the
     cube's boundary (id -1) and numbers the (G-2)^3 interior nodes
     lexicographically, so that A is the operator with homogeneous Dirichlet
-    conditions.
+    conditions.  perturb = delta > 0 moves every interior vertex of the
+    (K+1)^3 vertex grid by delta h times a seeded uniform[-1, 1) in each
+    coordinate (the cube's boundary vertices stay), giving general trilinear
+    hexahedra: verts() returns their corners (delta < 0.25 keeps every
+    Jacobian positive).
     """
 
     def __init__(self, K: int, N: int, seed: int | None = 1, permute: bool = True,
-                 dirichlet: bool = False):
+                 dirichlet: bool = False, perturb: float = 0.0):
         self.K, self.N = int(K), int(N)
         self.Nq = self.N + 1
         self.Np = self.Nq ** 3
@@ -108,6 +112,8 @@ class Mesh:
         self.G = self.K * self.N + 1
         self.NG = self.G ** 3
         self.h = 1.0 / self.K
+        self.perturb = float(perturb)
+        self.seed = seed
         if self.NL >= 2 ** 31 or self.NG >= 2 ** 31:
             raise ValueError("mesh too large for int32 indices")
         if permute and seed is not None:
@@ -128,6 +134,28 @@ class Mesh:
             self.NG = int(inner.sum())
         else:
             self.grid = np.arange(self.NG, dtype=np.int64)
+
+    def verts(self) -> np.ndarray:
+        """Corners [E, 8, 3] of the elements in storage order: corner
+        v = vx + 2 (vy + 2 vz) of the element in slot s sits at grid vertex
+        (ex + vx, ey + vy, ez + vz) of element perm[s], possibly perturbed."""
+        K, h = self.K, self.h
+        n1 = K + 1
+        g = np.arange(n1 ** 3, dtype=np.int64)
+        gv = np.stack([g % n1, (g // n1) % n1, g // (n1 * n1)], axis=1)
+        pos = gv.astype(np.float64) * h
+        if self.perturb > 0.0:
+            inner = np.all((gv > 0) & (gv < K), axis=1)
+            seed = 0 if self.seed is None else int(self.seed)
+            for d in range(3):
+                off = uniform(n1 ** 3, seed, 11 + d) * (self.perturb * h)
+                pos[:, d] = np.where(inner, pos[:, d] + off, pos[:, d])
+        ex, ey, ez = self.element_coords(self.perm)
+        out = np.empty((self.E, 8, 3))
+        for v in range(8):
+            vx, vy, vz = v & 1, (v >> 1) & 1, (v >> 2) & 1
+            out[:, v, :] = pos[(ex + vx) + n1 * ((ey + vy) + n1 * (ez + vz))]
+        return out
 
     def element_coords(self, e):
         """(ex, ey, ez) of natural element index e."""

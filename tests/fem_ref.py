@@ -72,3 +72,23 @@ def global_coords(mesh):
         return e * h + 0.5 * h * (r[i] + 1.0)
 
     return coord(gx), coord(gy), coord(gz)
+
+
+def node_coords(mesh):
+    """(x, y, z) of every global node through each element's trilinear map
+    x(r) = sum_v X_v (1 + sx r)(1 + sy s)(1 + sz t) / 8 of its corners
+    mesh.verts() (general hexahedra; equal to global_coords when unperturbed)."""
+    r, _, _ = gll_np(mesh.N)
+    Nq, Np = mesh.Nq, mesh.Np
+    l = np.arange(Np)
+    ri, rj, rk = r[l % Nq], r[(l // Nq) % Nq], r[l // (Nq * Nq)]
+    sh = np.empty((Np, 8))
+    for v in range(8):
+        sx, sy, sz = (1 if v & 1 else -1), (1 if v & 2 else -1), (1 if v & 4 else -1)
+        sh[:, v] = (1 + sx * ri) * (1 + sy * rj) * (1 + sz * rk) / 8.0
+    X = np.einsum("lv,evd->eld", sh, mesh.verts())
+    ids = mesh.ids.reshape(mesh.E, Np)
+    keep = ids >= 0
+    out = np.zeros((mesh.NG, 3))
+    out[ids[keep]] = X[keep]
+    return out[:, 0], out[:, 1], out[:, 2]

@@ -669,3 +669,86 @@ def test_dirichlet_manufactured_solution_converges_spectrally():
     e4, e6 = _manufactured(2, 4), _manufactured(2, 6)
     assert e6 < 1e-6
     assert e4 > 300 * e6
+
+
+# ------------------------------------------------- general (perturbed) hexahedra
+
+@pytest.mark.parametrize("K,N", [(2, 2), (3, 3), (2, 5)])
+def test_geo_operator_on_cubes_is_the_affine_operator(K, N):
+    """Undeformed corners through the general-geometry route (Jacobian,
+    cofactor inverse, w det J J^-1 J^-T) give the affine operator."""
+    m = synth.Mesh(K, N, seed=3)
+    coef = synth.lognormal(m.E, 2)
+    p = synth.uniform(m.NG, 5)
+    a = oracle.apply_A(m.E, N, m.h, 0.7, m.ids, m.NG, p, coef)
+    g = oracle.apply_A_geo(m.E, N, 0.7, m.verts(), m.ids, m.NG, p, coef)
+    assert np.abs(a - g).max() <= 1e-13 * np.abs(a).max()
+    np.testing.assert_allclose(oracle.diag_A_geo(m.E, N, 0.7, m.verts(), m.ids, m.NG, coef),
+                               oracle.diag_A(m.E, N, m.h, 0.7, m.ids, m.NG, coef), rtol=1e-13)
+
+
+@pytest.mark.parametrize("K,N", [(2, 2), (3, 3), (2, 4)])
+def test_geo_linear_fields_and_volume_are_exact(K, N):
+    """On a perturbed mesh of the unit cube (N >= 2, so that GLL quadrature
+    integrates det J, of degree 2 in each variable, exactly): 1^T M 1 = 1,
+    S 1 = 0, and for u = a . x, which the trilinear map keeps in the
+    discrete space, u^T S u = |a|^2 -- a check of J, its inverse, their
+    order and the weights together."""
+    m = synth.Mesh(K, N, seed=7, perturb=0.2)
+    V = m.verts()
+    one = np.ones(m.NG)
+    M1 = oracle.apply_A_geo(m.E, N, 1.0, V, m.ids, m.NG, one, coef=np.zeros(m.E))
+    assert abs(M1.sum() - 1.0) <= 1e-13
+    S1 = oracle.apply_A_geo(m.E, N, 0.0, V, m.ids, m.NG, one)
+    assert np.abs(S1).max() <= 1e-12
+    x, y, z = fem_ref.node_coords(m)
+    a = np.array([0.3, -1.1, 0.7])
+    u = a[0] * x + a[1] * y + a[2] * z
+    Su = oracle.apply_A_geo(m.E, N, 0.0, V, m.ids, m.NG, u)
+    assert abs(u @ Su - a @ a) <= 1e-12 * (a @ a)
+
+
+def test_geo_operator_is_invariant_under_rigid_motion():
+    """Rotating and translating every corner leaves w det J J^-1 J^-T and so
+    A unchanged; A stays symmetric and positive definite."""
+    m = synth.Mesh(2, 3, seed=5, perturb=0.22)
+    V = m.verts()
+    th = 0.7
+    Q = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0, 0, 1.0]])
+    Q = Q @ np.array([[1.0, 0, 0], [0, np.cos(0.4), -np.sin(0.4)], [0, np.sin(0.4), np.cos(0.4)]])
+    Vr = V @ Q.T + np.array([2.0, -1.0, 0.5])
+    coef = synth.lognormal(m.E, 3)
+    p = synth.uniform(m.NG, 9)
+    a = oracle.apply_A_geo(m.E, 3, 0.4, V, m.ids, m.NG, p, coef)
+    b = oracle.apply_A_geo(m.E, 3, 0.4, Vr, m.ids, m.NG, p, coef)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    A = np.stack([oracle.apply_A_geo(m.E, 3, 0.4, V, m.ids, m.NG, e, coef)
+                  for e in np.eye(m.NG)], axis=1)
+    np.testing.assert_allclose(A, A.T, atol=1e-12 * np.abs(A).max())
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+
+
+def test_geo_node_coords_match_the_structured_grid():
+    m = synth.Mesh(3, 4, seed=2)
+    for c, g in zip(fem_ref.node_coords(m), fem_ref.global_coords(m)):
+        np.testing.assert_allclose(c, g, atol=1e-15)
+
+
+def _manufactured_geo(K, N):
+    m = synth.Mesh(K, N, seed=1, dirichlet=True, perturb=0.2)
+    V = m.verts()
+    x, y, z = fem_ref.node_coords(m)
+    u = np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+    b = oracle.apply_A_geo(m.E, N, 1.0, V, m.ids, m.NG, 3 * np.pi ** 2 * u, coef=np.zeros(m.E))
+    uh, it, _, _, rr = oracle.cg_geo(m.E, N, 0.0, V, m.ids, m.NG, b, tol=1e-13, maxit=4000)
+    assert rr[-1] <= 1e-26 * rr[0]
+    return np.abs(uh - u).max()
+
+
+def test_geo_manufactured_solution_converges_spectrally():
+    """-Laplace u = f with u = 0 on the boundary of the unit cube, meshed by
+    perturbed hexahedra: the error falls below 1e-5 at N = 6 and more than
+    50 times from N = 4 to N = 6."""
+    e4, e6 = _manufactured_geo(2, 4), _manufactured_geo(2, 6)
+    assert e6 < 1e-5
+    assert e4 > 50 * e6
