@@ -158,6 +158,22 @@ int bs_problem_create(const bs_map *map, double h, double lambda,
                       const double *h_coef, bs_problem **prob);
 int bs_problem_destroy(bs_problem *prob);
 
+/* The same operator on general hexahedra (the non-affine geometric factors
+ * Sec. 5 allows for): element e is the trilinear image of [-1,1]^3 with
+ * corner v = vx + 2 (vy + 2 vz) (vx, vy, vz in {0,1}; vertex v sits at
+ * reference point (2vx-1, 2vy-1, 2vz-1)) at h_verts[24 e + 3 v + d],
+ * d = x, y, z (HOST, copied; E*24 doubles).  With J = dx/dr at each GLL node,
+ *   (A_e u)_n = c_e sum_q grad_r l_n(q)^T G_q grad_r u(q) + lambda M_n u_n,
+ *   G_q = w_q det J J^-1 J^-T,  M_n = w_n det J,
+ * G and M are computed here in FP64 and kept on the device (7 doubles per
+ * local node).  N <= 11.  BS_ERR_ARG if some element has det J <= 0 at a
+ * node.  Such a problem serves bs_apply_A, bs_apply_local, bs_diag_A and
+ * bs_cg_solve (FP64 operator; Jacobi, graphs, scattered storage); the
+ * float-float operator, the FP32 refined, batched and learned solvers
+ * return BS_ERR_ARG for it. */
+int bs_problem_create_geo(const bs_map *map, double lambda, const double *h_coef,
+                          const double *h_verts, bs_problem **prob);
+
 /* Ap = A p (N_G vectors). */
 int bs_apply_A(const bs_problem *prob, const double *p, double *Ap,
                void *stream);

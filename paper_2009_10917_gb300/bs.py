@@ -93,6 +93,7 @@ _SIGS = {
     "bs_scatter_f32": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bs_gather_f32": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bs_problem_create": (ctypes.c_int, [_vp, _d, _d, _vp, _pp]),
+    "bs_problem_create_geo": (ctypes.c_int, [_vp, _d, _vp, _vp, _pp]),
     "bs_problem_destroy": (ctypes.c_int, [_vp]),
     "bs_apply_A": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bs_apply_A_ff": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -304,9 +305,11 @@ class Map:
 # ---------------------------------------------------------------- operator and CG
 
 class Problem:
-    """A = Z^T (c S_L + lambda M_L) Z on a map (bs_problem)."""
+    """A = Z^T (c S_L + lambda M_L) Z on a map (bs_problem); verts (host
+    float64 [E, 8, 3], element corners) selects general hexahedra
+    (bs_problem_create_geo; h is then unused)."""
 
-    def __init__(self, m: Map, h: float, lam: float, coef=None):
+    def __init__(self, m: Map, h: float, lam: float, coef=None, verts=None):
         self.map = m  # keep the map alive
         self.h, self.lam = h, lam
         c = None
@@ -314,8 +317,13 @@ class Problem:
             self._coef = np.ascontiguousarray(coef, dtype=np.float64)
             c = self._coef.ctypes.data_as(ctypes.c_void_p)
         hd = ctypes.c_void_p()
-        _check(lib().bs_problem_create(m.handle, h, lam, c, ctypes.byref(hd)),
-               "bs_problem_create")
+        if verts is None:
+            _check(lib().bs_problem_create(m.handle, h, lam, c, ctypes.byref(hd)),
+                   "bs_problem_create")
+        else:
+            v = np.ascontiguousarray(verts, dtype=np.float64)
+            _check(lib().bs_problem_create_geo(m.handle, lam, c, v.ctypes.data_as(ctypes.c_void_p),
+                                               ctypes.byref(hd)), "bs_problem_create_geo")
         self.handle = hd
 
     def __del__(self):

@@ -822,6 +822,7 @@ static int check_batch(int32_t nsolves, const bs_problem *const *probs, const do
     BS_ARG(probs[s]->N + 1 <= kBMaxNq, "%s: problem %d has degree %d > %d", fn, s, probs[s]->N,
            kBMaxNq - 1);
     BS_ARG(probs[s]->map->NG > 0, "%s: problem %d is empty", fn, s);
+    BS_ARG(!probs[s]->d_geo, "%s: problem %d has geometric factors (not batched)", fn, s);
     for (int t = 0; t < s; ++t) BS_ARG(probs[t] != probs[s], "%s: problem %d repeats %d", fn, s, t);
     if (f32 && !probs[s]->d_f32) {
       bs_problem *p = const_cast<bs_problem *>(probs[s]);

@@ -572,6 +572,7 @@ int bs_mlp_pairs(const bs_problem *P, const double *d_r, int64_t count, const in
                  int32_t negate_odd, float *d_X, float *d_T, void *stream) {
   BS_ARG(P && P->map, "bs_mlp_pairs: problem is NULL");
   BS_ARG(count >= 0, "bs_mlp_pairs: count < 0");
+  BS_ARG(!P->d_geo, "bs_mlp_pairs: not available with geometric factors");
   BS_ARG(P->N >= 2 && P->N <= 8, "bs_mlp_pairs: degree %d outside 2..8", P->N);
   if (count == 0) return BS_OK;
   BS_ARG(d_r && d_elems && d_X && d_T, "bs_mlp_pairs: NULL argument");
@@ -614,6 +615,7 @@ int bs_fpcg_learned(const bs_problem *Pc, bs_mlp *mlp, const double *b, double *
   int dev = -1;
   BS_CUDA_TRY(cudaGetDevice(&dev));
   BS_ARG(dev == P->device, "bs_fpcg_learned: problem on another device");
+  BS_ARG(!P->d_geo, "bs_fpcg_learned: not available with geometric factors");
   BS_ARG(maxit >= 0 && tol >= 0.0 && std::isfinite(tol), "bs_fpcg_learned: bad tol or maxit");
   BS_ARG((flags & ~(BS_CG_GRAPH | BS_FPCG_ODD | BS_FPCG_NO_JUDGE | BS_CG_FF_OPERATOR)) == 0,
          "bs_fpcg_learned: unknown flags 0x%x", (unsigned)flags);

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "bs_op_ff.cuh"
@@ -122,6 +124,7 @@ static void free_problem(bs_problem *p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   cudaFree(p->d_coef);
+  cudaFree(p->d_geo);
   cudaFree(p->d_tab);
   cudaFree(p->d_tabf);
   cudaFree(p->d_tabff);
@@ -135,6 +138,38 @@ static void free_problem(bs_problem *p) {
   cudaFree(p->d_owner);
   if (p->h_state) cudaFreeHost(p->h_state);
   free(p);
+}
+
+// diag(A_L) per local node n = (i, j, k): the unit vector's quadratic form,
+//   c_e [sum_m D_mi^2 G_rr(m,j,k) + sum_m D_mj^2 G_ss(i,m,k) + sum_m D_mk^2 G_tt(i,j,m)
+//        + 2 (D_ii D_jj G_rs + D_ii D_kk G_rt + D_jj D_kk G_st)(n)] + lambda M_n
+// (grad_r l_n is nonzero only on the three lines through n, and two of its
+// components only at n itself).
+static __global__ void k_diag_geo(int64_t NL, int Nq, const OpTab<double> *__restrict__ tab,
+                           const double *__restrict__ coef, const double *__restrict__ geo,
+                           double lambda, double *__restrict__ out) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int Nq2 = Nq * Nq, Np = Nq2 * Nq;
+  const double *D = tab->D;
+  for (int64_t l = tid; l < NL; l += nth) {
+    const int64_t e = l / Np;
+    const int n = (int)(l - e * Np);
+    const int i = n % Nq, j = (n / Nq) % Nq, k = n / Nq2;
+    const int64_t b = e * Np;
+    double s = 0.0;
+    for (int m = 0; m < Nq; ++m) {
+      const double di = D[m * Nq + i], dj = D[m * Nq + j], dk = D[m * Nq + k];
+      s = fma(di * di, geo[b + m + Nq * j + Nq2 * k], s);
+      s = fma(dj * dj, geo[3 * NL + b + i + Nq * m + Nq2 * k], s);
+      s = fma(dk * dk, geo[5 * NL + b + i + Nq * j + Nq2 * m], s);
+    }
+    const double dii = D[i * Nq + i], djj = D[j * Nq + j], dkk = D[k * Nq + k];
+    s = fma(2.0 * dii * djj, geo[NL + l], s);
+    s = fma(2.0 * dii * dkk, geo[2 * NL + l], s);
+    s = fma(2.0 * djj * dkk, geo[4 * NL + l], s);
+    out[l] = fma(coef ? coef[e] : 1.0, s, lambda * geo[6 * NL + l]);
+  }
 }
 
 }  // namespace bs
@@ -196,6 +231,8 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
     split(w[i], tabff.wh[i], tabff.wl[i]);
     for (int m = 0; m < Nq; ++m) {
       tab.K[i * Nq + m] = K[i * Nq + m];
+      tab.D[i * Nq + m] = D[i * Nq + m];
+      tabf.D[i * Nq + m] = (float)D[i * Nq + m];
       tabf.K[i * Nq + m] = (float)K[i * Nq + m];
       split(K[i * Nq + m], tabff.Kh[i * Nq + m], tabff.Kl[i * Nq + m]);
       split(w[i] * w[m], tabff.Wh[i * Nq + m], tabff.Wl[i * Nq + m]);
@@ -231,6 +268,100 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
   return BS_OK;
 }
 
+int bs_problem_create_geo(const bs_map *map, double lambda, const double *h_coef,
+                          const double *h_verts, bs_problem **out) {
+  BS_ARG(out != nullptr, "bs_problem_create_geo: out is NULL");
+  *out = nullptr;
+  BS_ARG(map != nullptr, "bs_problem_create_geo: map is NULL");
+  BS_ARG(map->N + 1 <= kGeoMaxNq, "bs_problem_create_geo: degree %d > %d", map->N,
+         kGeoMaxNq - 1);
+  BS_ARG(map->E == 0 || h_verts != nullptr, "bs_problem_create_geo: verts is NULL");
+  const int N = map->N, Nq = N + 1, Np = Nq * Nq * Nq;
+  const int64_t E = map->E, NL = map->NL;
+  double x[kMaxNq], w[kMaxNq], D[kMaxNq * kMaxNq];
+  gll_tables(N, x, w, D);
+  // G = w det J J^-1 J^-T (upper triangle) and M = w det J at every node,
+  // J = dx/dr of the trilinear map of the element's eight corners
+  std::vector<double> fac((size_t)kGeoFactors * (size_t)NL);
+  // elements split over host threads; bad[t] is the first degenerate
+  // element thread t met (or -1)
+  const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<int64_t> bad((size_t)nth, -1);
+  auto work = [&](int t) {
+  for (int64_t e = t; e < E; e += nth) {
+    const double *X = h_verts + 24 * e;
+    for (int n = 0; n < Np; ++n) {
+      const int i = n % Nq, j = (n / Nq) % Nq, k = n / (Nq * Nq);
+      const double r = x[i], s = x[j], t = x[k];
+      double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int v = 0; v < 8; ++v) {
+        const double sx = (v & 1) ? 1.0 : -1.0, sy = (v & 2) ? 1.0 : -1.0,
+                     sz = (v & 4) ? 1.0 : -1.0;
+        const double dr = 0.125 * sx * (1.0 + sy * s) * (1.0 + sz * t);
+        const double ds = 0.125 * (1.0 + sx * r) * sy * (1.0 + sz * t);
+        const double dt = 0.125 * (1.0 + sx * r) * (1.0 + sy * s) * sz;
+        for (int d = 0; d < 3; ++d) {
+          J[d][0] += X[3 * v + d] * dr;
+          J[d][1] += X[3 * v + d] * ds;
+          J[d][2] += X[3 * v + d] * dt;
+        }
+      }
+      // adjugate: C[p][d] = cofactor, J^-1 = C / det (rows: reference p)
+      double C[3][3];
+      C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      C[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+      C[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+      C[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+      C[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+      C[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      C[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+      C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      const double det = J[0][0] * C[0][0] + J[0][1] * C[1][0] + J[0][2] * C[2][0];
+      if (!(det > 0.0) || !std::isfinite(det)) {
+        if (bad[(size_t)t] < 0) bad[(size_t)t] = e;
+        continue;
+      }
+      const double wq = w[i] * w[j] * w[k];
+      // w det J (C/det)(C/det)^T = (w / det) C C^T
+      const double sc = wq / det;
+      auto cc = [&](int p, int q) {
+        return C[p][0] * C[q][0] + C[p][1] * C[q][1] + C[p][2] * C[q][2];
+      };
+      const size_t l = (size_t)(e * Np + n);
+      fac[0 * (size_t)NL + l] = sc * cc(0, 0);
+      fac[1 * (size_t)NL + l] = sc * cc(0, 1);
+      fac[2 * (size_t)NL + l] = sc * cc(0, 2);
+      fac[3 * (size_t)NL + l] = sc * cc(1, 1);
+      fac[4 * (size_t)NL + l] = sc * cc(1, 2);
+      fac[5 * (size_t)NL + l] = sc * cc(2, 2);
+      fac[6 * (size_t)NL + l] = wq * det;
+    }
+  }
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+  }
+  for (int64_t b : bad)
+    if (b >= 0)
+      return fail(BS_ERR_ARG, "bs_problem_create_geo: element %lld is inverted or degenerate",
+                  (long long)b);
+  bs_problem *p = nullptr;
+  if (int rc = bs_problem_create(map, 1.0, lambda, h_coef, &p)) return rc;
+  cudaError_t err = cudaMalloc(&p->d_geo, sizeof(double) * (fac.size() + 1));
+  if (err == cudaSuccess && !fac.empty())
+    err = cudaMemcpy(p->d_geo, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    free_problem(p);
+    return fail(BS_ERR_CUDA, "bs_problem_create_geo: %s", cudaGetErrorString(err));
+  }
+  *out = p;
+  return BS_OK;
+}
+
 int bs_problem_destroy(bs_problem *p) {
   free_problem(p);
   return BS_OK;
@@ -241,6 +372,10 @@ int bs_apply_local(const bs_problem *p, const double *uL, double *AuL, void *str
   if (p->map->NL == 0) return BS_OK;
   BS_ARG(uL && AuL, "bs_apply_local: NULL vector");
   const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
+  if (p->d_geo)
+    return launch_ax_geo<false>(p->N, p->map->E, p->map->NL, nullptr, nullptr, uL, AuL,
+                                p->d_tab, p->d_coef, p->d_geo, p->lambda, nullptr,
+                                as_stream(stream));
   return launch_ax_local<double, false>(p->N, p->map->E, nullptr, nullptr, uL, AuL, p->d_tab,
                                         p->d_coef, g, mlam, nullptr, as_stream(stream));
 }
@@ -258,6 +393,7 @@ int bs_apply_A_ff(const bs_problem *p, const double *x, double *Ax, void *stream
   if (int rc = check_prob(p, "bs_apply_A_ff")) return rc;
   if (p->map->NG == 0) return BS_OK;
   BS_ARG(x && Ax, "bs_apply_A_ff: NULL vector");
+  BS_ARG(!p->d_geo, "bs_apply_A_ff: not available with geometric factors");
   const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
   return apply_A_global<double, false, EpNone>(p, true, p->d_tab, x, Ax, p->d_ApL, g, mlam,
                                                EpNone{}, nullptr, as_stream(stream));
@@ -271,8 +407,12 @@ int bs_diag_A(const bs_problem *p, double *d_diag, void *stream) {
   cudaStream_t s = as_stream(stream);
   if (p->map->NL > 0) {
     const int grid = stream_grid(p->map->NL, 1, kStreamBlock, 8);
-    k_diag_local<double><<<grid, kStreamBlock, 0, s>>>(p->map->NL, p->N + 1, p->d_tab, p->d_coef,
-                                                      g, mlam, p->d_ApL);
+    if (p->d_geo)
+      k_diag_geo<<<grid, kStreamBlock, 0, s>>>(p->map->NL, p->N + 1, p->d_tab, p->d_coef,
+                                               p->d_geo, p->lambda, p->d_ApL);
+    else
+      k_diag_local<double><<<grid, kStreamBlock, 0, s>>>(p->map->NL, p->N + 1, p->d_tab,
+                                                        p->d_coef, g, mlam, p->d_ApL);
     BS_LAUNCH_CHECK();
   }
   return launch_gather<double, false, EpNone>(p->map, p->d_ApL, d_diag, nullptr, nullptr,

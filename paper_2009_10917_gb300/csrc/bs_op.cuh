@@ -39,6 +39,7 @@ constexpr int kMaxNq = 16;  // degrees 1..15
 template <typename T>
 struct OpTab {
   T K[kMaxNq * kMaxNq];  // K[i*Nq + m] = (D^T W D)_im
+  T D[kMaxNq * kMaxNq];  // D[a*Nq + i] = l_i'(r_a), the GLL derivative matrix
   T w[kMaxNq];           // GLL weights
   // Even-odd halves of Kh = W^-1 K (centrosymmetric; even Nq only), h = Nq/2:
   // Ee[a*h + m] = (Kh_am + Kh_a,Nq-1-m) / 2, Eo[a*h + m] = (Kh_am - Kh_a,Nq-1-m) / 2.
@@ -430,6 +431,7 @@ struct bs_problem {
   int32_t N;
   double h, lambda;
   double *d_coef;                 // [E] or NULL
+  double *d_geo;                  // [7 NL] geometric factors of general hexahedra, or NULL
   bs::OpTab<double> *d_tab;       // FP64 tables
   bs::OpTab<float> *d_tabf;       // FP32 tables
   bs::OpTabFF *d_tabff;           // float-pair tables of the float-float operator

@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "bs_op.cuh"
+#include "bs_op_geo.cuh"
 
 namespace bs {
 
@@ -491,6 +492,18 @@ template <typename T, bool DOT, class Ep>
 int apply_A_global(const bs_problem *P, bool ff, const OpTab<T> *tab, const T *p, T *Ap, T *ApL,
                    T g, T mlam, Ep ep, const CgState *st, cudaStream_t s) {
   const bs_map *m = P->map;
+  if (P->d_geo) {  // general hexahedra: FP64, unfused
+    if constexpr (std::is_same<T, double>::value) {
+      if (ff) return fail(BS_ERR_ARG, "the float-float operator has no geometric factors");
+      if (int rc = launch_ax_geo<true>(P->N, m->E, m->NL, m->d_elem_order, m->d_ids, p, ApL,
+                                       P->d_tab, P->d_coef, P->d_geo, P->lambda, st, s))
+        return rc;
+      return launch_gather_rows<T, DOT, Ep>(m, false, ApL, Ap, DOT ? p : nullptr,
+                                            P->d_partials, P->d_counter, nullptr, 0, ep, st, s);
+    } else {
+      return fail(BS_ERR_ARG, "FP32 operator not available with geometric factors");
+    }
+  }
   const bool fused = g_op_fusion != 0;
   const int32_t *ids = fused ? m->d_ids_f : m->d_ids;
   double *opp = fused && DOT ? P->d_op_partials : nullptr;

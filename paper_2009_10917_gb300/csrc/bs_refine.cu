@@ -177,6 +177,7 @@ extern "C" int bs_cg_solve_refined_f32(const bs_problem *Pc, const double *b, do
   BS_CUDA_TRY(cudaGetDevice(&dev));
   BS_ARG(dev == P->device, "bs_cg_solve_refined_f32: problem belongs to device %d", P->device);
   BS_ARG(maxit >= 0 && outer_maxit >= 0, "bs_cg_solve_refined_f32: negative limit");
+  BS_ARG(!P->d_geo, "bs_cg_solve_refined_f32: not available with geometric factors");
   BS_ARG(tol >= 0.0 && std::isfinite(tol), "bs_cg_solve_refined_f32: bad tol");
   BS_ARG(inner_tol > 0.0 && inner_tol < 1.0, "bs_cg_solve_refined_f32: inner_tol in (0, 1)");
   const bs_map *m = P->map;
