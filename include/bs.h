@@ -214,8 +214,9 @@ int bs_apply_A_ff(const bs_problem *prob, const double *p, double *Ap, void *str
  *   centrosymmetric W^-1 K (Solomonoff's decomposition; half-length
  *   contractions, about a quarter fewer operations per node); results
  *   differ by rounding only.
- * Returns the previous mode; a negative value only queries it.  Not
- * thread-safe against solves in flight. */
+ * Problems with geometric factors (bs_problem_create_geo) always use their
+ * own unfused FP64 kernel.  Returns the previous mode; a negative value only
+ * queries it.  Not thread-safe against solves in flight. */
 enum { BS_OP_FUSED = 1, BS_OP_DIRECT = 2 };
 int bs_operator_mode(int32_t mode);
 

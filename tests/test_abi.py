@@ -54,3 +54,35 @@ def test_argument_errors_without_gpu():
     assert L.bs_copy(4, None, None, None) == 1
     L.bs_last_error.restype = ctypes.c_char_p
     assert b"NULL" in L.bs_last_error()
+
+
+def test_header_constants_match_the_binding():
+    """Every BS_* enum value of include/bs.h that the Python binding names
+    has the same value there."""
+    from paper_2009_10917_gb300 import bs
+    text = open(os.path.join(ROOT, "include", "bs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\b(BS_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    named = [k for k in consts if hasattr(bs, k)]
+    assert len(named) >= 20
+    for k in named:
+        assert getattr(bs, k) == consts[k], k
+    for k in ("BS_CG_SCATTERED", "BS_OP_FUSED", "BS_OP_DIRECT", "BS_CG_FF_OPERATOR"):
+        assert k in named
+
+
+def test_operator_mode_and_geometry_arguments_without_gpu():
+    """The operator-mode switch is host state; bs_problem_create_geo
+    validates its arguments before any CUDA call."""
+    from paper_2009_10917_gb300 import build
+    L = ctypes.CDLL(build.build())
+    L.bs_operator_mode.argtypes = [ctypes.c_int32]
+    assert L.bs_operator_mode(-1) == 0          # default: unfused, even-odd
+    assert L.bs_operator_mode(3) == 0           # fused | direct
+    assert L.bs_operator_mode(-1) == 3
+    assert L.bs_operator_mode(0) == 3
+    L.bs_problem_create_geo.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert L.bs_problem_create_geo(None, 1.0, None, None, ctypes.byref(out)) == 1
+    assert L.bs_problem_create_geo(None, 1.0, None, None, None) == 1
