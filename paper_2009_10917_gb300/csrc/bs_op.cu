@@ -255,8 +255,9 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
   if (e == cudaSuccess) e = cudaMemset(p->d_state, 0, sizeof(CgState));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_partials, sizeof(double) * kMaxPartials + 256);
   if (e == cudaSuccess) e = cudaMemset(p->d_partials, 0, sizeof(double) * kMaxPartials + 256);
-  if (e == cudaSuccess)
-    e = cudaMalloc(&p->d_op_partials, sizeof(double) * (ax_blocks(N, map->E) + 1));
+  // one partial per element-kernel block: at most one block per element,
+  // whichever kernel form (direct, even-odd) a later call selects
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_op_partials, sizeof(double) * (map->E + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_state, sizeof(CgState));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {

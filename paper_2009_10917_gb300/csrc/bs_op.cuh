@@ -439,7 +439,7 @@ struct bs_problem {
   double *d_vec;                  // 6 x [NG]: r, p, Ap, z, dinv, spare
   bs::CgState *d_state;
   double *d_partials;             // [kMaxPartials]
-  double *d_op_partials;          // [ax_blocks(N, E)] the fused operator's block partials
+  double *d_op_partials;          // [E + 1] the fused operator's block partials (<= E blocks)
   unsigned int *d_counter;
   bs::CgState *h_state;           // pinned host mirror for convergence checks
   cudaStream_t cap_stream;        // private stream for graph capture

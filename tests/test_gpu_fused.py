@@ -180,3 +180,21 @@ def test_evenodd_fp32_refined_and_scattered(fusion):
     x, info = P.cg_refined_f32(b, tol=1e-10)
     r = bh - oracle.apply_A(m.E, 7, m.h, 1.0, m.ids, m.NG, x.cpu().numpy())
     assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(bh)
+
+
+def test_fused_on_a_problem_created_under_another_mode(fusion):
+    """The fused operator's per-block partials hold one value per element,
+    enough for any element-kernel form: a problem made while the direct form
+    was selected (4 elements per block at N = 7) runs fused with the
+    even-odd form (2 per block)."""
+    bs.operator_mode(bs.BS_OP_DIRECT)
+    m = synth.Mesh(5, 7, seed=3)
+    Z = bs.Map(m.E, 7, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, 1.0)
+    bs.operator_mode(0)
+    bh = synth.uniform(m.NG, 4)
+    b = cuda(bh)
+    (xa, ia), (xb, ib) = both(lambda: P.cg(b, tol=1e-10, maxit=3000, flags=bs.BS_CG_GRAPH))
+    assert abs(ia["iterations"] - ib["iterations"]) <= 1
+    r = bh - oracle.apply_A(m.E, 7, m.h, 1.0, m.ids, m.NG, xa.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(bh)
