@@ -455,7 +455,8 @@ static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, c
 static int capture_chunk(bs_problem *P, double *x, bool precond, bool ff, bool scat,
                          int chunk) {
   const void *key[4] = {x, (const void *)(intptr_t)((precond ? 1 : 0) | (ff ? 2 : 0) |
-                                                     (g_op_fusion ? 4 : 0) | (scat ? 8 : 0)),
+                                                     (g_op_fusion ? 4 : 0) | (scat ? 8 : 0) |
+                                                     (g_op_evenodd ? 16 : 0)),
                         (const void *)(intptr_t)chunk,
                         (const void *)P->map};
   if (P->graph && key[0] == P->graph_key[0] && key[1] == P->graph_key[1] &&

@@ -132,7 +132,8 @@ static int f32_iteration(const bs_problem *P, cudaStream_t s) {
 }
 
 static int capture_f32(bs_problem *P, int chunk) {
-  const void *key[4] = {nullptr, (const void *)(intptr_t)(2 | (g_op_fusion ? 4 : 0)),
+  const void *key[4] = {nullptr, (const void *)(intptr_t)(2 | (g_op_fusion ? 4 : 0) |
+                                                    (g_op_evenodd ? 16 : 0)),
                         (const void *)(intptr_t)chunk,
                         (const void *)P->map};
   if (P->graph && memcmp(key, P->graph_key, sizeof(key)) == 0) return BS_OK;
