@@ -752,3 +752,63 @@ def test_geo_manufactured_solution_converges_spectrally():
     e4, e6 = _manufactured_geo(2, 4), _manufactured_geo(2, 6)
     assert e6 < 1e-5
     assert e4 > 50 * e6
+
+
+def test_perturbed_mesh_is_conforming_and_keeps_the_boundary():
+    """Corners of neighbouring elements that share a grid vertex coincide
+    (the trilinear elements stay conforming), boundary vertices stay on the
+    cube, interior ones move by at most delta h per coordinate, and delta = 0
+    gives the structured grid."""
+    K, delta = 3, 0.2
+    m0, m = synth.Mesh(K, 2, seed=4), synth.Mesh(K, 2, seed=4, perturb=delta)
+    V0, V = m0.verts(), m.verts()
+    ex, ey, ez = m.element_coords(m.perm)
+    pos = {}
+    for s in range(m.E):
+        for v in range(8):
+            key = (ex[s] + (v & 1), ey[s] + ((v >> 1) & 1), ez[s] + ((v >> 2) & 1))
+            np.testing.assert_allclose(V0[s, v], np.array(key) / K, atol=1e-15)
+            if key in pos:
+                assert np.array_equal(pos[key], V[s, v])
+            pos[key] = V[s, v]
+            d = V[s, v] - V0[s, v]
+            if any(c in (0, K) for c in key):
+                assert np.all(d == 0.0)
+            assert np.all(np.abs(d) <= delta / K)
+    assert len(pos) == (K + 1) ** 3
+
+
+def test_scattered_storage_cg_is_global_cg():
+    """Reading of the scattered form (Sec. 3): CG on Z A x = Z b with every
+    vector kept as Z v, A p = Z Z^T A_L p_L and inner products over the
+    lowest copy of each node, built here from the oracle's scatter, gather
+    and element operator, takes global CG's steps (the oracle's Algorithm 1)
+    to rounding."""
+    m = synth.Mesh(3, 3, seed=6)
+    b = synth.uniform(m.NG, 2)
+    _, _, al, be, rr = oracle.cg(m.E, 3, m.h, 1.0, m.ids, m.NG, b, maxit=25, fixed_iters=True)
+    owner = np.zeros(m.NL, bool)
+    seen = set()
+    for l, g in enumerate(m.ids):
+        if g >= 0 and g not in seen:
+            owner[l] = True
+            seen.add(g)
+    dot = lambda u, v: float(np.sum(u[owner] * v[owner]))
+    Z = lambda vG: oracle.scatter(m.ids, vG, np.zeros(m.NL))
+    r = Z(b)
+    p = r.copy()
+    x = np.zeros(m.NL)
+    rho = dot(r, r)
+    for j in range(25):
+        w = oracle.apply_local(m.E, 3, m.h, 1.0, p)
+        Ap = Z(oracle.gather(m.ids, w, m.NG))
+        alpha = rho / dot(p, Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        rho_new = dot(r, r)
+        beta = rho_new / rho
+        p = r + beta * p
+        rho = rho_new
+        assert abs(alpha - al[j]) <= 1e-11 * abs(al[j])
+        assert abs(beta - be[j]) <= 1e-11 * abs(be[j])
+        assert abs(rho - rr[j + 1]) <= 1e-11 * rr[j + 1]
