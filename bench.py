@@ -6,7 +6,7 @@ of the streaming sweep: copy, AXPY, norm, inner product and the fused CG
 update on FP64 vectors of 2^28 entries (2 GiB each, far larger than L2), then
 scatter and gather on the degree-7, 48^3 structured hex mesh with permuted
 elements (110592 elements, 56.6M local and 38.3M global nodes).  `value` is
-the algorithmic bytes of the step (SURVEY-style counts: copy 16n, AXPY 24n,
+the algorithmic bytes of the step (what each operation must move: copy 16n, AXPY 24n,
 norm 8n, dot 16n, CG update 48n, scatter 12 N_L + 8 N_G, gather
 12 N_L + 12 N_G + 4) divided by the device time, i.e. the effective HBM GB/s
 of the whole step.  Per-operation GB/s and fractions of the measured HBM peak
