@@ -812,3 +812,18 @@ def test_scattered_storage_cg_is_global_cg():
         assert abs(alpha - al[j]) <= 1e-11 * abs(al[j])
         assert abs(beta - be[j]) <= 1e-11 * abs(be[j])
         assert abs(rho - rr[j + 1]) <= 1e-11 * rr[j + 1]
+
+
+def test_input_generator_is_splitmix64():
+    """The seeded inputs come from splitmix64 as published: its first three
+    outputs from state 0 (tests/golden/splitmix64_state0.txt), and uniform
+    values in [-1, 1) built from the top 53 bits."""
+    want = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_state0.txt"))
+            if l.startswith("0x")]
+    z = np.array([(k * int(synth.GAMMA)) % (1 << 64) for k in (1, 2, 3)], dtype=np.uint64)
+    assert [int(v) for v in synth._mix(z)] == want
+    u = synth.uniform(1 << 16, 3)
+    assert u.min() >= -1.0 and u.max() < 1.0 and abs(u.mean()) < 0.01
+    b = synth.bits(4, 3, 5)
+    assert np.array_equal(((b >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) * 2.0 - 1.0,
+                          synth.uniform(4, 3, 5))
