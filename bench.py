@@ -367,9 +367,10 @@ def operator_times(P, p, reps=20):
 def geo_section(Z, m, b, N, K, delta=0.2):
     """The same solve on general hexahedra: every interior vertex of the mesh
     moved by up to delta h (seeded), the operator built from the
-    non-affine geometric factors (bs_problem_create_geo).  FP64 CG to 1e-8
-    after a 16-iteration warm-up, the true residual with the same operator,
-    and the device time of one A p against the affine even-odd operator."""
+    non-affine geometric factors (bs_problem_create_geo).  FP64 CG to 1e-8,
+    with the FP64 and with the float-float element kernel, each after a
+    16-iteration warm-up, the true residual with the FP64 operator, and the
+    device time of one A p (both kernels) against the affine even-odd one."""
     import time
 
     import torch
@@ -379,24 +380,28 @@ def geo_section(Z, m, b, N, K, delta=0.2):
     mg = synth.Mesh(K, N, seed=1, perturb=delta)
     Pg = bs.Problem(Z, mg.h, 1.0, verts=mg.verts())
     setup = time.perf_counter() - t0
-    Pg.cg(b, tol=1e-8, maxit=16, flags=bs.BS_CG_GRAPH | bs.BS_CG_FIXED_ITERS)
-    x, info = Pg.cg(b, tol=1e-8, maxit=100000, flags=bs.BS_CG_GRAPH)
-    r = Pg.apply_A(x)
-    bs.axpy(1.0, b, -1.0, r)
-    out = {"perturb": delta, "setup_seconds": round(setup, 3),
-           "fp64_cg": {"seconds": round(info["seconds"], 4), "iterations": info["iterations"],
-                       "rel_residual_true_fp64": torch.linalg.norm(r).item() /
-                       torch.linalg.norm(b).item()}}
+    out = {"perturb": delta, "setup_seconds": round(setup, 3)}
+    for name, fl in (("fp64_cg", 0), ("fp64_cg_ff_operator", bs.BS_CG_FF_OPERATOR)):
+        Pg.cg(b, tol=1e-8, maxit=16, flags=bs.BS_CG_GRAPH | bs.BS_CG_FIXED_ITERS | fl)
+        x, info = Pg.cg(b, tol=1e-8, maxit=100000, flags=bs.BS_CG_GRAPH | fl)
+        r = Pg.apply_A(x)
+        bs.axpy(1.0, b, -1.0, r)
+        out[name] = {"seconds": round(info["seconds"], 4), "iterations": info["iterations"],
+                     "rel_residual_true_fp64": torch.linalg.norm(r).item() /
+                     torch.linalg.norm(b).item()}
+    out["speedup_ff_vs_fp64_cg"] = round(out["fp64_cg"]["seconds"] /
+                                         out["fp64_cg_ff_operator"]["seconds"], 3)
     Ap = torch.empty_like(b)
     Pa = bs.Problem(Z, m.h, 1.0)
-    for name, P in (("geo", Pg), ("affine_evenodd", Pa)):
+    for name, fn in (("geo", Pg.apply_A), ("geo_ff", Pg.apply_A_ff),
+                     ("affine_evenodd", Pa.apply_A)):
         for _ in range(3):
-            P.apply_A(b, Ap)
+            fn(b, Ap)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
         for _ in range(10):
-            P.apply_A(b, Ap)
+            fn(b, Ap)
         e1.record()
         torch.cuda.synchronize()
         out.setdefault("operator_ms", {})[name] = round(e0.elapsed_time(e1) / 10, 4)

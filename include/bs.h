@@ -167,10 +167,11 @@ int bs_problem_destroy(bs_problem *prob);
  *   G_q = w_q det J J^-1 J^-T,  M_n = w_n det J,
  * G and M are computed here in FP64 and kept on the device (7 doubles per
  * local node).  N <= 11.  BS_ERR_ARG if some element has det J <= 0 at a
- * node.  Such a problem serves bs_apply_A, bs_apply_local, bs_diag_A and
- * bs_cg_solve (FP64 operator; Jacobi, graphs, scattered storage); the
- * float-float operator, the FP32 refined, batched and learned solvers
- * return BS_ERR_ARG for it. */
+ * node.  Such a problem serves bs_apply_A, bs_apply_local, bs_diag_A,
+ * bs_apply_A_ff and bs_cg_solve (FP64 or float-float element kernel, the
+ * latter splitting the factors into float pairs on the fly; Jacobi, graphs,
+ * scattered storage); the FP32 refined, batched and learned solvers return
+ * BS_ERR_ARG for it. */
 int bs_problem_create_geo(const bs_map *map, double lambda, const double *h_coef,
                           const double *h_verts, bs_problem **prob);
 

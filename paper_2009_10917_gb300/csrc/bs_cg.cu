@@ -385,8 +385,11 @@ static int scat_iteration(const bs_problem *P, bool precond, bool ff, cudaStream
   CgState *st = P->d_state;
   const double g = 0.5 * P->h, mlam = P->lambda * g * g * g;
   int rc = P->d_geo
-               ? launch_ax_geo<false>(P->N, m->E, m->NL, nullptr, nullptr, L.p, P->d_ApL,
-                                      P->d_tab, P->d_coef, P->d_geo, P->lambda, st, s)
+               ? (ff ? launch_ax_geo_ff<false>(P->N, m->E, m->NL, nullptr, nullptr, L.p,
+                                               P->d_ApL, P->d_tabff, P->d_coef, P->d_geo,
+                                               P->lambda, st, s)
+                     : launch_ax_geo<false>(P->N, m->E, m->NL, nullptr, nullptr, L.p, P->d_ApL,
+                                            P->d_tab, P->d_coef, P->d_geo, P->lambda, st, s))
            : ff ? launch_ax_local_ff<false>(P->N, m->E, nullptr, nullptr, L.p, P->d_ApL,
                                             P->d_tabff, P->d_coef, g, mlam, st, s)
                 : launch_ax_local<double, false>(P->N, m->E, nullptr, nullptr, L.p, P->d_ApL,
@@ -504,8 +507,6 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
   BS_ARG(dev == P->device, "bs_cg_solve: problem belongs to device %d", P->device);
   BS_ARG(maxit >= 0, "bs_cg_solve: maxit < 0");
   BS_ARG(tol >= 0.0 && std::isfinite(tol), "bs_cg_solve: tol must be finite and >= 0");
-  BS_ARG(!(P->d_geo && (flags & BS_CG_FF_OPERATOR)),
-         "bs_cg_solve: the float-float operator has no geometric factors");
   const bs_map *m = P->map;
   const int64_t NG = m->NG;
   BS_ARG(NG == 0 || (b && x), "bs_cg_solve: NULL vector");

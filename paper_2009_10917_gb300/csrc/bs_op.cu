@@ -233,6 +233,7 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
       tab.K[i * Nq + m] = K[i * Nq + m];
       tab.D[i * Nq + m] = D[i * Nq + m];
       tabf.D[i * Nq + m] = (float)D[i * Nq + m];
+      split(D[i * Nq + m], tabff.Dh[i * Nq + m], tabff.Dl[i * Nq + m]);
       tabf.K[i * Nq + m] = (float)K[i * Nq + m];
       split(K[i * Nq + m], tabff.Kh[i * Nq + m], tabff.Kl[i * Nq + m]);
       split(w[i] * w[m], tabff.Wh[i * Nq + m], tabff.Wl[i * Nq + m]);
@@ -394,7 +395,6 @@ int bs_apply_A_ff(const bs_problem *p, const double *x, double *Ax, void *stream
   if (int rc = check_prob(p, "bs_apply_A_ff")) return rc;
   if (p->map->NG == 0) return BS_OK;
   BS_ARG(x && Ax, "bs_apply_A_ff: NULL vector");
-  BS_ARG(!p->d_geo, "bs_apply_A_ff: not available with geometric factors");
   const double g = 0.5 * p->h, mlam = p->lambda * g * g * g;
   return apply_A_global<double, false, EpNone>(p, true, p->d_tab, x, Ax, p->d_ApL, g, mlam,
                                                EpNone{}, nullptr, as_stream(stream));

@@ -38,6 +38,8 @@ struct OpTabFF {
   float Kh[kMaxNq * kMaxNq], Kl[kMaxNq * kMaxNq];
   float Wh[kMaxNq * kMaxNq], Wl[kMaxNq * kMaxNq];
   float wh[kMaxNq], wl[kMaxNq];
+  // the GLL derivative matrix D as float pairs (general hexahedra)
+  float Dh[kMaxNq * kMaxNq], Dl[kMaxNq * kMaxNq];
   // the even-odd halves OpTab::Ee, OpTab::Eo as float pairs
   float Eeh[(kMaxNq / 2) * (kMaxNq / 2)], Eel[(kMaxNq / 2) * (kMaxNq / 2)];
   float Eoh[(kMaxNq / 2) * (kMaxNq / 2)], Eol[(kMaxNq / 2) * (kMaxNq / 2)];
@@ -481,6 +483,149 @@ int launch_ax_local_ff(int N, int64_t E, const int32_t *order, const int32_t *id
   return BS_OK;
 }
 
+// ---------------------------------------------------------------- general hexahedra
+
+// The general-hexahedron operator of bs_op_geo.cuh in float-float
+// arithmetic: u, D and the six factors of every node split into float pairs
+// (the factors on the fly, by integer operations), the gradient, the flux
+// G grad u and the transposed derivative accumulated by ff_fma, the mass term
+// from one FP64 product lambda M per node; the result joined into a double.
+// Same thread mapping and phases as k_ax_geo.
+template <int NQ, bool GATHER_IN>
+__global__ void __launch_bounds__(GeoShape<NQ>::THREADS)
+    k_ax_geo_ff(int64_t E, int64_t NL, const int32_t *__restrict__ order,
+                const int32_t *__restrict__ ids, const double *__restrict__ in,
+                double *__restrict__ out, const OpTabFF *__restrict__ tab,
+                const double *__restrict__ coef, const double *__restrict__ geo, double lambda,
+                const CgState *st) {
+  using S = GeoShape<NQ>;
+  constexpr int NQ2 = S::NQ2, NP = S::NP;
+  __shared__ float s_uh[S::EPB * NP], s_ul[S::EPB * NP];
+  __shared__ float s_frh[S::EPB * NP], s_frl[S::EPB * NP];
+  __shared__ float s_fsh[S::EPB * NP], s_fsl[S::EPB * NP];
+  __shared__ float s_Dh[NQ2], s_Dl[NQ2];
+  if (cg_halted(st)) return;
+  for (int t = threadIdx.x; t < NQ2; t += blockDim.x) {
+    s_Dh[t] = tab->Dh[t];
+    s_Dl[t] = tab->Dl[t];
+  }
+  const int le = threadIdx.x / NQ2;
+  const int ij = threadIdx.x - le * NQ2;
+  const int i = ij % NQ, j = ij / NQ;
+  const int64_t slot = (int64_t)blockIdx.x * S::EPB + le;
+  const bool active = le < S::EPB && slot < E;
+  const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  const int off = (le < S::EPB ? le : 0) * NP;
+  float *uh = s_uh + off, *ul = s_ul + off;
+  float *frh = s_frh + off, *frl = s_frl + off, *fsh = s_fsh + off, *fsl = s_fsl + off;
+  float rh[NQ], rl[NQ];
+  if (active) {
+    const int64_t base = e * NP + ij;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      double v;
+      if (GATHER_IN) {
+        const int32_t id = __ldcs(ids + base + k * NQ2);
+        v = id >= 0 ? in[id] : 0.0;
+      } else {
+        v = __ldcs(in + base + k * NQ2);
+      }
+      const FF f = ff_split(v);
+      rh[k] = f.hi;
+      rl[k] = f.lo;
+      uh[ij + k * NQ2] = f.hi;
+      ul[ij + k * NQ2] = f.lo;
+    }
+  }
+  __syncthreads();
+  FF ft[NQ];
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      FF ur{0.f, 0.f}, us{0.f, 0.f}, ut{0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) {
+        const int lr = m + NQ * j + NQ2 * k, ls = i + NQ * m + NQ2 * k;
+        ff_fma(ur, s_Dh[i * NQ + m], s_Dl[i * NQ + m], uh[lr], ul[lr]);
+        ff_fma(us, s_Dh[j * NQ + m], s_Dl[j * NQ + m], uh[ls], ul[ls]);
+        ff_fma(ut, s_Dh[k * NQ + m], s_Dl[k * NQ + m], rh[m], rl[m]);
+      }
+      const int64_t l = e * NP + ij + k * NQ2;
+      const FF g0 = ff_split(__ldcs(geo + l)), g1 = ff_split(__ldcs(geo + NL + l));
+      const FF g2 = ff_split(__ldcs(geo + 2 * NL + l)), g3 = ff_split(__ldcs(geo + 3 * NL + l));
+      const FF g4 = ff_split(__ldcs(geo + 4 * NL + l)), g5 = ff_split(__ldcs(geo + 5 * NL + l));
+      FF fr{0.f, 0.f}, fs{0.f, 0.f}, fq{0.f, 0.f};
+      ff_fma(fr, g0.hi, g0.lo, ur.hi, ur.lo);
+      ff_fma(fr, g1.hi, g1.lo, us.hi, us.lo);
+      ff_fma(fr, g2.hi, g2.lo, ut.hi, ut.lo);
+      ff_fma(fs, g1.hi, g1.lo, ur.hi, ur.lo);
+      ff_fma(fs, g3.hi, g3.lo, us.hi, us.lo);
+      ff_fma(fs, g4.hi, g4.lo, ut.hi, ut.lo);
+      ff_fma(fq, g2.hi, g2.lo, ur.hi, ur.lo);
+      ff_fma(fq, g4.hi, g4.lo, us.hi, us.lo);
+      ff_fma(fq, g5.hi, g5.lo, ut.hi, ut.lo);
+      frh[ij + k * NQ2] = fr.hi;
+      frl[ij + k * NQ2] = fr.lo;
+      fsh[ij + k * NQ2] = fs.hi;
+      fsl[ij + k * NQ2] = fs.lo;
+      ft[k] = fq;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const FF cg = ff_split(coef ? coef[e] : 1.0);
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    FF acc{0.f, 0.f};
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int lr = m + NQ * j + NQ2 * k, ls = i + NQ * m + NQ2 * k;
+      ff_fma(acc, s_Dh[m * NQ + i], s_Dl[m * NQ + i], frh[lr], frl[lr]);
+      ff_fma(acc, s_Dh[m * NQ + j], s_Dl[m * NQ + j], fsh[ls], fsl[ls]);
+      ff_fma(acc, s_Dh[m * NQ + k], s_Dl[m * NQ + k], ft[m].hi, ft[m].lo);
+    }
+    const int64_t l = e * NP + ij + k * NQ2;
+    const FF lm = ff_split(lambda * __ldcs(geo + 6 * NL + l));
+    FF o{0.f, 0.f};
+    ff_fma(o, cg.hi, cg.lo, acc.hi, acc.lo);
+    ff_fma(o, lm.hi, lm.lo, rh[k], rl[k]);
+    __stcs(out + l, ff_widen(o.hi) + ff_widen(o.lo));
+  }
+}
+
+template <bool GATHER_IN>
+int launch_ax_geo_ff(int N, int64_t E, int64_t NL, const int32_t *order, const int32_t *ids,
+                     const double *in, double *out, const OpTabFF *tab, const double *coef,
+                     const double *geo, double lambda, const CgState *st, cudaStream_t s) {
+  if (E == 0) return BS_OK;
+#define BS_AXGF_CASE(NQ)                                                                 \
+  case NQ: {                                                                             \
+    using Sh = GeoShape<NQ>;                                                             \
+    const int64_t grid = (E + Sh::EPB - 1) / Sh::EPB;                                    \
+    k_ax_geo_ff<NQ, GATHER_IN><<<(unsigned)grid, Sh::THREADS, 0, s>>>(                   \
+        E, NL, order, ids, in, out, tab, coef, geo, lambda, st);                         \
+    break;                                                                               \
+  }
+  switch (N + 1) {
+    BS_AXGF_CASE(2)
+    BS_AXGF_CASE(3)
+    BS_AXGF_CASE(4)
+    BS_AXGF_CASE(5)
+    BS_AXGF_CASE(6)
+    BS_AXGF_CASE(7)
+    BS_AXGF_CASE(8)
+    BS_AXGF_CASE(9)
+    BS_AXGF_CASE(10)
+    BS_AXGF_CASE(11)
+    BS_AXGF_CASE(12)
+    default:
+      return fail(BS_ERR_ARG, "degree %d unsupported with geometric factors", N);
+  }
+#undef BS_AXGF_CASE
+  BS_LAUNCH_CHECK();
+  return BS_OK;
+}
+
 // 1: A p through the fused element kernel and the gather of the shared rows;
 // 0 (the default): element kernel, then the gather of every row.
 extern int g_op_fusion;
@@ -492,11 +637,13 @@ template <typename T, bool DOT, class Ep>
 int apply_A_global(const bs_problem *P, bool ff, const OpTab<T> *tab, const T *p, T *Ap, T *ApL,
                    T g, T mlam, Ep ep, const CgState *st, cudaStream_t s) {
   const bs_map *m = P->map;
-  if (P->d_geo) {  // general hexahedra: FP64, unfused
+  if (P->d_geo) {  // general hexahedra: FP64 or float-float, unfused
     if constexpr (std::is_same<T, double>::value) {
-      if (ff) return fail(BS_ERR_ARG, "the float-float operator has no geometric factors");
-      if (int rc = launch_ax_geo<true>(P->N, m->E, m->NL, m->d_elem_order, m->d_ids, p, ApL,
-                                       P->d_tab, P->d_coef, P->d_geo, P->lambda, st, s))
+      if (int rc = ff ? launch_ax_geo_ff<true>(P->N, m->E, m->NL, m->d_elem_order, m->d_ids, p,
+                                               ApL, P->d_tabff, P->d_coef, P->d_geo, P->lambda,
+                                               st, s)
+                      : launch_ax_geo<true>(P->N, m->E, m->NL, m->d_elem_order, m->d_ids, p, ApL,
+                                            P->d_tab, P->d_coef, P->d_geo, P->lambda, st, s))
         return rc;
       return launch_gather_rows<T, DOT, Ep>(m, false, ApL, Ap, DOT ? p : nullptr,
                                             P->d_partials, P->d_counter, nullptr, 0, ep, st, s);

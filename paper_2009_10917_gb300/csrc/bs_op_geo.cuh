@@ -16,7 +16,7 @@
 // fluxes in shared memory and the t flux in registers.  About 6 (N+1) + 12
 // FP64 operations and 56 bytes of factors per local node: FP64-pipe bound on
 // GB300 (the factors alone would take 0.5 ms of HBM time at N = 7 on 48^3).
-// Degrees 1..11.
+// Degrees 1..11.  A float-float form of the same kernel is in bs_op_ff.cuh.
 #pragma once
 
 #include "bs_op.cuh"

@@ -54,6 +54,20 @@ def test_geo_apply_matches_oracle(K, N):
     np.testing.assert_allclose(d, oracle.diag_A_geo(m.E, N, 0.5, V, m.ids, m.NG, c), rtol=1e-12)
 
 
+@pytest.mark.parametrize("K,N", [(3, 1), (3, 3), (2, 4), (2, 7), (1, 11)])
+def test_geo_float_float_apply_matches_oracle(K, N):
+    """The float-float general-geometry kernel: every value a float pair
+    (about 2^-46 relative per term), so within 1e-11 max|A p| of the oracle,
+    at unit scale and scaled by 2^-60 (its inputs stay inside the float-pair
+    window)."""
+    m, Z, P, c, V = make(K, N)
+    for scale in (1.0, 2.0 ** -60):
+        p = synth.uniform(m.NG, 5) * scale
+        got = P.apply_A_ff(cuda(p)).cpu().numpy()
+        want = oracle.apply_A_geo(m.E, N, 0.5, V, m.ids, m.NG, p, c)
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
 def test_geo_on_cubes_matches_the_affine_problem():
     m, Z, P, c, V = make(3, 5, delta=0.0)
     Pa = bs.Problem(Z, m.h, 0.5, c)
@@ -89,7 +103,9 @@ def _oracle_iterations(jacobi):
 
 
 @pytest.mark.parametrize("flags", [0, bs.BS_CG_GRAPH, bs.BS_CG_JACOBI, bs.BS_CG_SCATTERED,
-                                   bs.BS_CG_JACOBI | bs.BS_CG_SCATTERED | bs.BS_CG_GRAPH])
+                                   bs.BS_CG_JACOBI | bs.BS_CG_SCATTERED | bs.BS_CG_GRAPH,
+                                   bs.BS_CG_FF_OPERATOR | bs.BS_CG_GRAPH,
+                                   bs.BS_CG_FF_OPERATOR | bs.BS_CG_JACOBI | bs.BS_CG_SCATTERED])
 def test_geo_cg_to_tolerance(flags):
     m, Z, P, c, V = make(4, 5, coef=False)
     bh = synth.uniform(m.NG, 2)
@@ -120,10 +136,6 @@ def test_geo_manufactured_solution():
 def test_geo_rejections():
     m, Z, P, c, V = make(2, 3)
     b = cuda(synth.uniform(m.NG, 1))
-    with pytest.raises(bs.BSError):
-        P.cg(b, flags=bs.BS_CG_FF_OPERATOR)
-    with pytest.raises(bs.BSError):
-        P.apply_A_ff(b)
     with pytest.raises(bs.BSError):
         P.cg_refined_f32(b)
     with pytest.raises(bs.BSError):
