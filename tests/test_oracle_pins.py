@@ -827,3 +827,14 @@ def test_input_generator_is_splitmix64():
     b = synth.bits(4, 3, 5)
     assert np.array_equal(((b >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) * 2.0 - 1.0,
                           synth.uniform(4, 3, 5))
+
+
+def test_batched_workload_specs():
+    """The batched workload: 256 (N, K) pairs, N uniform in 2..8 and K in
+    4..24 (every value drawn), seeded and reproducible; the sum of N_G the
+    bench reports for seed 7."""
+    specs = synth.batched_specs(256, 7)
+    assert specs == synth.batched_specs(256, 7) and len(specs) == 256
+    Ns, Ks = zip(*specs)
+    assert set(Ns) == set(range(2, 9)) and set(Ks) <= set(range(4, 25)) and len(set(Ks)) >= 18
+    assert sum((k * n + 1) ** 3 for n, k in specs) == 157354317
