@@ -1,0 +1,196 @@
+"""GPU parity at the sizes and in the launch configuration the benchmark times.
+
+The streaming kernels run a grid fixed per device (SMs x resident blocks), so
+the per-thread work grows with n: at a million entries each thread runs its
+main loop once or twice, while at n = 2^28 it runs about a hundred trips,
+and the FP64 norm flushes its float-pair accumulators into double a few dozen
+times.  Those long per-thread chains, the grid-stride tails and the gather's
+and scatter's full tile lists only run at large sizes, so this file compares
+them with the oracle there:
+
+- BS1, BS2, BS5 (x and r): bitwise, at n = 2^24, 2^26 + 3 and 2^28 (the
+  benchmark's vectors), with aligned and misaligned starts;
+- BS3, BS4 and the r.r of BS5: within 1e-13 relative of the oracle's Dot2
+  sum (the bound of Table 1's reductions for FP64; the GPU's order has an
+  error of about (terms per thread + log2 of the grid) eps sum|x y| / |x.y|,
+  which for uniform[-1, 1) inputs stays below 1e-14 at these n);
+- FP32 twins at 2^24 + 3: copy, AXPY, update bitwise, reductions within
+  2^-40 sum |x y| (float-pair accumulation keeps about 44 bits);
+- BS6, BS7: bitwise on the degree-7 24^3 mesh (7.1M local nodes), on a
+  degree-1 and a degree-15 mesh of about 33M local nodes, with masked entries,
+  and on the benchmark's degree-7 48^3 mesh (56.6M local, 38.3M global nodes);
+- the learned network's forward pass element by element (per-entry bound
+  derived from the bf16 rounding of the hidden layer).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_10917_gb300 import bs, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def bits(a):
+    return np.ascontiguousarray(a).view(np.uint64 if a.dtype == np.float64 else np.uint32)
+
+
+def dev(a, off=0):
+    """Device copy of a, starting `off` elements into a fresh buffer."""
+    t = torch.empty(a.size + off, dtype=torch.from_numpy(a[:0]).dtype, device="cuda")
+    t[off:] = torch.from_numpy(a).cuda()
+    return t[off:]
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+LARGE = [(1 << 24, 0, 0), (1 << 24, 1, 1), (1 << 24, 0, 1), ((1 << 26) + 3, 0, 0),
+         ((1 << 26) + 3, 1, 0)]
+
+
+@pytest.mark.parametrize("n,ox,oy", LARGE)
+def test_large_copy_axpy_norm_dot(n, ox, oy):
+    x, y = synth.uniform(n, 31, 0), synth.uniform(n, 31, 1)
+    xd = dev(x, ox)
+    yd = dev(y, oy)
+    nr = bs.norm(xd).cpu().numpy()
+    s, sq = oracle.norm(x)
+    assert rel(nr[0], s) <= 1e-13 and rel(nr[1], sq) <= 1e-13
+    d = bs.dot(xd, yd).cpu().numpy()[0]
+    assert abs(d - oracle.dot(x, y)) <= 1e-13 * abs(oracle.dot(x, y))
+    bs.axpy(0.5, xd, 1.0, yd)
+    assert np.array_equal(bits(yd.cpu().numpy()), bits(oracle.axpy(0.5, x, 1.0, y)))
+    c = dev(np.zeros(n), oy)
+    bs.copy(xd, c)
+    assert np.array_equal(bits(c.cpu().numpy()), bits(x))
+
+
+@pytest.mark.parametrize("n,off", [(1 << 24, 0), ((1 << 26) + 3, 1)])
+def test_large_cg_update(n, off):
+    p, Ap, x, r = (synth.uniform(n, 32, s) for s in range(4))
+    xd, rd = dev(x, off), dev(r, off)
+    rr = bs.cg_update(0.37, dev(p, off), dev(Ap, off), xd, rd).cpu().numpy()[0]
+    xo, ro, rro = oracle.cg_update(0.37, p, Ap, x, r)
+    assert np.array_equal(bits(xd.cpu().numpy()), bits(xo))
+    assert np.array_equal(bits(rd.cpu().numpy()), bits(ro))
+    assert rel(rr, rro) <= 1e-13
+
+
+def test_benchmark_size_streaming_ops():
+    """BS1-BS5 on the benchmark's 2^28-entry vectors (2 GiB each), with the
+    benchmark's alpha = 0.5 and beta = 1, through the same calls."""
+    n = 1 << 28
+    x, y = synth.uniform(n, 1, 0), synth.uniform(n, 1, 1)
+    xd, yd = dev(x), dev(y)
+    del y
+    ws = bs.workspace()
+    red = torch.zeros(4, dtype=torch.float64, device="cuda")
+    c = torch.empty_like(xd)
+    bs.copy(xd, c)
+    assert torch.equal(c, xd)
+    del c
+    bs.axpy(0.5, xd, 1.0, yd)
+    bs.norm(xd, red[0:2], ws)
+    bs.dot(xd, yd, red[2:3], ws)
+    yh = yd.cpu().numpy()
+    del yd
+    y2 = oracle.axpy(0.5, x, 1.0, synth.uniform(n, 1, 1))
+    assert np.array_equal(bits(yh), bits(y2))
+    del y2
+    s, sq = oracle.norm(x)
+    r = red.cpu().numpy()
+    assert rel(r[0], s) <= 1e-13 and rel(r[1], sq) <= 1e-13
+    o = oracle.dot(x, yh)
+    assert abs(r[2] - o) <= 1e-13 * abs(o)
+    del x, xd, yh
+    torch.cuda.empty_cache()
+    p, Ap, xc, rv = (synth.uniform(n, 2, s) for s in range(4))
+    pd, Apd, xcd, rd = dev(p), dev(Ap), dev(xc), dev(rv)
+    bs.cg_update(0.5, pd, Apd, xcd, rd, red[3:4], ws)
+    del pd, Apd
+    xo, ro, rro = oracle.cg_update(0.5, p, Ap, xc, rv)
+    assert np.array_equal(bits(xcd.cpu().numpy()), bits(xo))
+    assert np.array_equal(bits(rd.cpu().numpy()), bits(ro))
+    assert rel(red[3].item(), rro) <= 1e-13
+    del xcd, rd
+    torch.cuda.empty_cache()
+
+
+def test_large_f32_twins():
+    n = (1 << 24) + 3
+    x = synth.uniform(n, 33, 0).astype(np.float32)
+    y = synth.uniform(n, 33, 1).astype(np.float32)
+    xd, yd = dev(x, 1), dev(y, 1)
+    d = bs.dot(xd, yd).cpu().numpy()[0]
+    scale = float(np.abs(x.astype(np.float64) * y.astype(np.float64)).sum())
+    assert abs(d - oracle.dot_f32(x, y)) <= 2.0 ** -40 * scale
+    nr = bs.norm(xd).cpu().numpy()
+    assert abs(nr[0] - oracle.dot_f32(x, x)) <= 2.0 ** -40 * oracle.dot_f32(x, x)
+    bs.axpy(-1.3, xd, -0.25, yd)
+    assert np.array_equal(bits(yd.cpu().numpy()), bits(oracle.axpy_f32(-1.3, x, -0.25, y)))
+    p, Ap, xx, r = (synth.uniform(n, 34, s).astype(np.float32) for s in range(4))
+    xxd, rd = dev(xx), dev(r)
+    rr = bs.cg_update(np.float32(0.37), dev(p), dev(Ap), xxd, rd).cpu().numpy()[0]
+    xo, ro, rro = oracle.cg_update_f32(np.float32(0.37), p, Ap, xx, r)
+    assert np.array_equal(bits(xxd.cpu().numpy()), bits(xo))
+    assert np.array_equal(bits(rd.cpu().numpy()), bits(ro))
+    assert abs(rr - rro) <= 2.0 ** -40 * rro
+
+
+# (K, N, masked fraction): the degree-7 24^3 mesh, degree 1 and 15 at about
+# 33M local nodes, and the benchmark's degree-7 48^3 mesh
+MESHES = [(24, 7, 0.0), (24, 7, 0.05), (160, 1, 0.0), (20, 15, 0.03), (48, 7, 0.0)]
+
+
+@pytest.mark.parametrize("K,N,frac", MESHES)
+def test_large_scatter_gather(K, N, frac):
+    m = synth.Mesh(K, N, seed=K + N)
+    ids = m.ids
+    if frac > 0:
+        ids = ids.copy()
+        ids[synth.uniform(ids.size, 35, 0, 0.0, 1.0) < frac] = -1
+    Z = bs.Map(m.E, N, m.NG, ids)
+    qG = synth.uniform(m.NG, 36)
+    init = np.full(m.NL, -3.5)
+    qL = dev(init)
+    Z.scatter(dev(qG), qL)
+    want = oracle.scatter(ids, qG, init)
+    assert np.array_equal(bits(qL.cpu().numpy()), bits(want))
+    del qL, want
+    ql = synth.uniform(m.NL, 37)
+    g = Z.gather(dev(ql)).cpu().numpy()
+    assert np.array_equal(bits(g), bits(oracle.gather(ids, ql, m.NG)))
+    del Z
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("odd", [False, True])
+def test_forward_element_by_element(split, odd):
+    """Each output entry of the network against the oracle run in the same
+    precision mode.  S_bi = sum_j |W2_ij| |a_bj|, with a the hidden values the
+    entry is built from (relu(W1 x) for f; W1 x / 2 for the odd part), bounds
+    how far the entry moves when hidden values change: the two sides round
+    hidden sums accumulated in different FP32 orders, so a hidden value may
+    land one bf16 ulp (2^-7 relative) apart, i.e. |dY| <= 2^-7 S.  In BF16x3
+    mode the rounding is to hi + lo pairs (about 2^-16 relative): |dY| <=
+    2^-14 S.  A wrong entry is off by about |Y|, which is S / 16 here."""
+    D, H, B = 216, 256, 2000
+    W1 = (synth.uniform(H * D, 40, 0).reshape(H, D) * np.sqrt(3.0 / D)).astype(np.float32)
+    W2 = (synth.uniform(D * H, 40, 1).reshape(D, H) * np.sqrt(3.0 / H)).astype(np.float32)
+    X = synth.uniform(B * D, 41).reshape(B, D).astype(np.float32)
+    net = bs.MLP(W1, W2, split=split)
+    Y = net.forward(torch.from_numpy(X).cuda(), odd=odd).cpu().numpy()
+    prec = oracle.PREC_BF16X3 if split else oracle.PREC_BF16
+    Yo, _ = oracle.mlp_forward(W1, W2, X, prec=prec, odd=odd)
+    h = X.astype(np.float64) @ W1.T.astype(np.float64)
+    a = 0.5 * np.abs(h) if odd else np.maximum(h, 0.0)
+    S = a @ np.abs(W2.T.astype(np.float64))
+    bound = (2.0 ** -14 if split else 2.0 ** -7) * S
+    err = np.abs(Y - Yo)
+    assert np.all(err <= bound), float((err / np.maximum(S, 1e-300)).max())
+    # and the entries agree closely almost everywhere (a flip is rare)
+    assert np.mean(err <= 1e-5 * S) >= 0.9
