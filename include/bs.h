@@ -141,6 +141,38 @@ int bs_gather(const bs_map *map, const double *qL, double *qG, void *stream);
 int bs_scatter_f32(const bs_map *map, const float *qG, float *qL, void *stream);
 int bs_gather_f32(const bs_map *map, const float *qL, float *qG, void *stream);
 
+/* ------------------------------------------------------------ BS6 over several ranks */
+
+/* The device steps of a gather whose elements are split over ranks (Sec. 3
+ * leaves the multi-rank gather/scatter aside as the non-trivial parallel
+ * implementation; the exchange plan and the messages are host-side, in the
+ * Python package's dist module).  Each rank owns a contiguous range of the
+ * element storage order and a bs_map of its elements onto the global nodes
+ * they touch (numbered rank-locally).  A node held by several ranks is summed
+ * as a chain in rank order: the first holder's ordinary bs_gather, then each
+ * later holder continues the serial sum from the partial it receives
+ * (bs_gather_rows with `start`), so the last holder gets bitwise the
+ * single-domain BS6 value (ascending local index), and sends it back.
+ *
+ * bs_rows: a set of `nrows` distinct rows (rank-local global-node indices in
+ * [0, NG)) of a map's Z^T, in the order of a message.  Host array copied;
+ * the map must outlive the row set.  Errors: BS_ERR_ARG (NULL, out of range,
+ * repeated row), BS_ERR_CUDA. */
+typedef struct bs_rows bs_rows;
+int bs_rows_create(const bs_map *map, int64_t nrows, const int32_t *h_rows,
+                   bs_rows **out);
+int bs_rows_destroy(bs_rows *rows);
+/* For i < nrows, g = rows[i]: qG[g] = start[i] + qL[l_1] + qL[l_2] + ...
+ * over g's local copies in ascending l, added one at a time; with start ==
+ * NULL the sum begins from +0.0 exactly as bs_gather does.  Other entries of
+ * qG are untouched.  start (DEVICE, nrows doubles) may be NULL. */
+int bs_gather_rows(const bs_rows *rows, const double *qL, const double *start,
+                   double *qG, void *stream);
+/* buf[i] = qG[rows[i]] (pack) and qG[rows[i]] = buf[i] (unpack); buf is a
+ * DEVICE array of nrows doubles.  Bitwise moves. */
+int bs_rows_pack(const bs_rows *rows, const double *qG, double *buf, void *stream);
+int bs_rows_unpack(const bs_rows *rows, const double *buf, double *qG, void *stream);
+
 /* ------------------------------------------------------------ operator */
 
 /* The Helmholtz operator A = Z^T (S_L + lambda M_L) Z of eqs. global_system,
@@ -352,6 +384,22 @@ int bs_cg_batched_autotune(int32_t nsolves, const bs_problem *const *probs,
                            bs_batched_config *best, double *ms_per_iteration,
                            void *stream);
 
+/* bs_set_wait_budget: the limit, in SM clock cycles, on every grid-barrier
+ * wait of the batched solver's cooperative kernel, on the CURRENT device.
+ * The paper has no counterpart: the bound is part of this library's failure
+ * handling (a device-side wait that could spin forever gives up instead).
+ * When a wait exceeds the budget the kernel records BS_ERR_TIMEOUT, every
+ * block returns (a block that passed the barrier meets the next one and gives
+ * up in turn), and bs_cg_solve_batched / bs_cg_batched_autotune return
+ * BS_ERR_TIMEOUT with the solves' results undefined; the next call starts
+ * from fresh barrier state.  cycles <= 0 restores the default, 2^32 cycles
+ * (about 2 s at 2 GHz; cooperative launches keep every block resident, so a
+ * healthy barrier never comes near it).  The old budget goes to *previous
+ * (may be NULL).  Synchronous; call it while no batched solve is running on
+ * the device.  The tcgen05 GEMM's mbarrier waits keep their own fixed limit.
+ * Errors: BS_ERR_CUDA. */
+int bs_set_wait_budget(int64_t cycles, int64_t *previous);
+
 /* ------------------------------------------------------------ learned preconditioner */
 
 /* A per-element network for a flexible PCG preconditioner.  The paper has no
@@ -479,9 +527,11 @@ int bs_fpcg_learned(const bs_problem *prob, bs_mlp *mlp, const double *b, double
  *    contents; the counter is cleared on `stream` at the start of each call.
  *    Calls that overlap on the GPU (on different streams, or from several
  *    threads) race on the array and give wrong results: serialise them.
- *  - Returns BS_ERR_ARG if the launch would need more than
- *    BS_NOALLOC_MAX_PARTIALS partials (a device with more resident blocks
- *    than that), or on the argument errors of bs_dot. */
+ *  - The grid never exceeds BS_NOALLOC_MAX_PARTIALS blocks (the kernel is
+ *    grid-stride, so any n fits); on a device with fewer resident blocks than
+ *    that the result is bitwise the one of bs_dot.
+ *  - Returns BS_ERR_ARG on the argument errors of bs_dot (n < 0, NULL output,
+ *    NULL vectors with n > 0). */
 int bs_dot_noalloc(int64_t n, const double *x, const double *y, double *d_out,
                    void *stream);
 
