@@ -35,7 +35,11 @@ constexpr int kBBlock = 256;
 constexpr int kBMaxNq = 9;                       // degrees 1..8 in a batch
 constexpr int kBSmem = 2187;                     // max EPB * Nq^3 for Nq <= 9 (>= kTileNnz)
 constexpr int kBChunk = 4096;                    // default vector entries per C/D item
-constexpr long long kBarrierBudget = 1ll << 32;  // clock cycles (~2 s) per barrier wait
+constexpr long long kBarrierBudget = 1ll << 32;  // default clock cycles (~2 s) per barrier wait
+
+// The barrier budget in force on this device (bs_set_wait_budget); read by
+// every grid barrier, so a change also reaches launches replayed from graphs.
+__device__ long long g_barrier_budget = kBarrierBudget;
 
 struct BDesc {
   int NQ;
@@ -95,9 +99,10 @@ __device__ bool grid_sync(unsigned int *bar, int *err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
+      const long long budget = *(volatile long long *)&g_barrier_budget;
       const long long t0 = clock64();
       while (*vgen == gen) {
-        if (clock64() - t0 > kBarrierBudget) {
+        if (clock64() - t0 > budget) {
           atomicExch(err, (int)BS_ERR_TIMEOUT);
           ok = 0;
           break;
@@ -1037,6 +1042,19 @@ int bs_cg_solve_batched_ex(int32_t nsolves, const bs_problem *const *probs,
                            int32_t flags, const bs_batched_config *cfg, bs_cg_info *infos,
                            void *stream) {
   return solve_batched(nsolves, probs, b, x, tol, maxit, flags, cfg, infos, stream);
+}
+
+int bs_set_wait_budget(int64_t cycles, int64_t *previous) {
+  long long prev = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&prev, g_barrier_budget, sizeof(prev));
+  if (e != cudaSuccess)
+    return fail(BS_ERR_CUDA, "bs_set_wait_budget: read: %s", cudaGetErrorString(e));
+  const long long v = cycles > 0 ? (long long)cycles : kBarrierBudget;
+  e = cudaMemcpyToSymbol(g_barrier_budget, &v, sizeof(v));
+  if (e != cudaSuccess)
+    return fail(BS_ERR_CUDA, "bs_set_wait_budget: write: %s", cudaGetErrorString(e));
+  if (previous) *previous = prev;
+  return BS_OK;
 }
 
 int bs_cg_batched_autotune(int32_t nsolves, const bs_problem *const *probs,
