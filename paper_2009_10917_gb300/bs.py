@@ -302,6 +302,45 @@ class Map:
         return qG
 
 
+class Rows:
+    """A set of distinct rows of a map's Z^T in message order (bs_rows): the
+    device steps of the multi-rank gather -- the continued row sums, and
+    packing / unpacking row values into message buffers."""
+
+    def __init__(self, m: Map, rows):
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        L = _bind(["bs_rows_create", "bs_rows_destroy", "bs_gather_rows", "bs_rows_pack",
+                   "bs_rows_unpack"])
+        h = ctypes.c_void_p()
+        _check(L.bs_rows_create(m.handle, rows.size, rows.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.byref(h)), "bs_rows_create")
+        self.handle, self.map, self.n = h, m, int(rows.size)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bs_rows_destroy(self.handle)
+            self.handle = None
+
+    def gather(self, qL, qG, start=None):
+        """qG[rows[i]] = start[i] (or +0) + the row's copies in ascending order."""
+        _check(lib().bs_gather_rows(self.handle, _ptr(qL, name="qL"), _ptr(start, name="start"),
+                                    _ptr(qG, name="qG"), _stream()), "bs_gather_rows")
+        return qG
+
+    def pack(self, qG, out=None):
+        """out[i] = qG[rows[i]]."""
+        out = torch.empty(self.n, dtype=torch.float64, device=qG.device) if out is None else out
+        _check(lib().bs_rows_pack(self.handle, _ptr(qG, name="qG"), _ptr(out, name="buf"),
+                                  _stream()), "bs_rows_pack")
+        return out
+
+    def unpack(self, buf, qG):
+        """qG[rows[i]] = buf[i]."""
+        _check(lib().bs_rows_unpack(self.handle, _ptr(buf, name="buf"), _ptr(qG, name="qG"),
+                                    _stream()), "bs_rows_unpack")
+        return qG
+
+
 # ---------------------------------------------------------------- operator and CG
 
 class Problem:
@@ -439,6 +478,16 @@ def solve_batched(problems, bs_, xs, tol=1e-8, maxit=1000000, flags=0, check=Tru
     return rc, [infos[i].as_dict() for i in range(n)]
 
 
+def set_wait_budget(cycles=0):
+    """bs_set_wait_budget: the batched solver's grid-barrier wait limit in SM
+    clock cycles on the current device (cycles <= 0: the default).  Returns
+    the previous limit."""
+    L = _bind(["bs_set_wait_budget"])
+    prev = ctypes.c_int64(0)
+    _check(L.bs_set_wait_budget(int(cycles), ctypes.byref(prev)), "bs_set_wait_budget")
+    return prev.value
+
+
 def autotune_batched(problems, bs_, flags=0, iters=4):
     """bs_cg_batched_autotune: returns (BatchedConfig, ms per iteration)."""
     n, P, B, _ = _arrays(problems, bs_)
@@ -455,6 +504,12 @@ def autotune_batched(problems, bs_, flags=0, iters=4):
 # ---------------------------------------------------------------- learned preconditioner
 
 _SIGS.update({
+    "bs_rows_create": (ctypes.c_int, [_vp, _i64, _vp, _pp]),
+    "bs_rows_destroy": (ctypes.c_int, [_vp]),
+    "bs_gather_rows": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "bs_rows_pack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_rows_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bs_set_wait_budget": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "bs_gemm_engine": (ctypes.c_int, [_i32]),
     "bs_mlp_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _pp]),
     "bs_mlp_destroy": (ctypes.c_int, [_vp]),
