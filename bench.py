@@ -50,10 +50,16 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-tolerance runs")
     ap.add_argument("--workload", default="stream",
-                    choices=["stream", "cg", "batched", "learned"],
+                    choices=["stream", "cg", "batched", "learned", "sweep"],
                     help="stream: the BS step (default); cg: only the CG solves on --cg-mesh; "
                          "batched: 256 uneven solves, batched vs one at a time; "
-                         "learned: learned-preconditioner FPCG vs Jacobi-PCG and plain CG")
+                         "learned: learned-preconditioner FPCG vs Jacobi-PCG and plain CG; "
+                         "sweep: BS1-BS7 over sizes and the T0/Wmax fit of Sec. 4")
+    ap.add_argument("--sweep-per-octave", type=int, default=4,
+                    help="sweep: log-spaced vector lengths per factor of two")
+    ap.add_argument("--sweep-runs", type=int, default=20,
+                    help="sweep: back-to-back runs per size")
+    ap.add_argument("--sweep-out", default=None, help="sweep: also write the JSON here")
     ap.add_argument("--learned-mesh", default="5,64", help="N,K of the learned workload")
     ap.add_argument("--no-plain", action="store_true",
                     help="learned workload: skip the (long) unpreconditioned CG solve")
@@ -85,7 +91,9 @@ def config(args, n, N, K, NL, NG):
     return {"workload": f"BS1-BS5 FP64 n=2^{args.log2n}; BS6/BS7 N={N} on {K}^3 hex mesh "
                         f"(N_L={NL}, N_G={NG}), permuted elements",
             "n": n, "degree": N, "mesh_K": K, "N_L": NL, "N_G": NG, "alpha": 0.5, "beta": 1.0,
-            "l2": "inputs larger than L2 (2 GiB vectors); no flush needed",
+            "l2": (f"inputs larger than L2 ({8 * n / 2 ** 20:.0f} MiB vectors); no flush needed"
+                   if 8 * n > 256 * 2 ** 20 else
+                   f"{8 * n / 2 ** 20:.1f} MiB vectors: partly L2-resident between steps"),
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -300,7 +308,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(args)
+        cpu = cpu_baseline(args, host, mesh)
     cg = learned = batched = None
     if not (args.no_cg and args.no_learned and args.no_batched):
         del dev, y, qL, qG2
@@ -643,6 +651,156 @@ def learned_section(args, compact=False):
     return out
 
 
+def _sweep_time(calls, runs, flush):
+    """Device time (s) per run of `runs` back-to-back calls, captured in one
+    CUDA graph (launch cost on the device only) and replayed after an L2
+    flush; calls(k) issues run k."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        calls(0)  # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for k in range(runs):
+            calls(k)
+    best = None
+    for _ in range(3):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3 / runs
+        best = t if best is None else min(best, t)
+    del g
+    return best
+
+
+def sweep_section(args):
+    """The streaming sweep of Sec. 6.2 on this GPU.  BS1-BS5 on FP64 vectors
+    of n = 2^10 .. 2^28 entries (log-spaced, --sweep-per-octave sizes per
+    factor of two, the powers of two among them), each timed as --sweep-runs
+    back-to-back calls through the C ABI captured in a CUDA graph, best of
+    three replays, after an L2 flush: once on the SAME buffers every run (what
+    a solver does; small vectors then live in L2) and once ROTATING through
+    distinct buffers (each run reads memory no earlier run touched, so every
+    size comes from HBM).  Each op's (bytes, seconds) pairs are fitted by least
+    squares to T(B) = T0 + B / Wmax (eq. time_model), with the Fischer-Brown
+    point B_0.8 = 4 T0 Wmax.  BS6/BS7: degree N = 1..15 on K^3 meshes of about
+    8e7 local nodes (K = round(cbrt(8e7) / (N + 1))), and the degree-7 K-sweep
+    that Table 2's BS6/BS7 fits use."""
+    import numpy as np
+    import torch
+
+    from paper_2009_10917_gb300 import bs, perfmodel, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    runs = args.sweep_runs
+    peak, peak_kind = peaks()
+    flush = torch.empty(256 << 20, dtype=torch.float32, device="cuda")  # 1 GiB > L2
+    ppo = max(1, args.sweep_per_octave)
+    ns = sorted({int(round(2.0 ** (10 + i / ppo))) for i in range(18 * ppo + 1)})
+    nmax = 1 << 28
+    pool_n = max(nmax, runs * (1 << 23))
+    host = synth.uniform(pool_n, 1, 0)
+    pools = [torch.from_numpy(host).cuda()]
+    del host
+    for k in range(1, 4):  # the other roles: shifted copies of the same values
+        pools.append(torch.roll(pools[0], 7919 * k))
+    red = torch.zeros(4, dtype=torch.float64, device="cuda")
+    ws = bs.workspace()
+    B_of = {"copy": 16, "axpy": 24, "norm": 8, "dot": 16, "cg_update": 48}
+
+    def views(n, k, rotate):
+        """The four role vectors of run k: distinct slices when rotating and
+        the whole set still fits the pools, else the first slice."""
+        off = k * n if rotate and (k + 1) * n <= pool_n else 0
+        return [p[off:off + n] for p in pools]
+
+    def op_call(op, n, rotate):
+        def calls(k):
+            a, b, c, d = views(n, k, rotate)
+            if op == "copy":
+                bs.copy(a, b)
+            elif op == "axpy":
+                bs.axpy(0.5, a, 1.0, b)
+            elif op == "norm":
+                bs.norm(a, red[0:2], ws)
+            elif op == "dot":
+                bs.dot(a, b, red[2:3], ws)
+            else:
+                bs.cg_update(1e-3, a, b, c, d, red[3:4], ws)
+        return calls
+
+    streaming = {}
+    for op in ("copy", "axpy", "norm", "dot", "cg_update"):
+        res = {"same_buffers": [], "rotating": []}
+        for n in ns:
+            for mode, rot in (("same_buffers", False), ("rotating", True)):
+                t = _sweep_time(op_call(op, n, rot), runs, flush)
+                res[mode].append([n, B_of[op] * n, t])
+        for mode in ("same_buffers", "rotating"):
+            B = np.array([r[1] for r in res[mode]], dtype=np.float64)
+            T = np.array([r[2] for r in res[mode]], dtype=np.float64)
+            t0, w = perfmodel.fit(B, T)
+            res[mode + "_fit"] = {"T0_us": round(t0 * 1e6, 3), "Wmax_GBs": round(w / 1e9, 1),
+                                  "Wmax_frac": round(w / 1e9 / peak, 4),
+                                  "B08_MiB": round(perfmodel.fischer_brown(t0, w) / 2 ** 20, 2)}
+            big = B >= 64 * 2 ** 20
+            res[mode + "_min_frac_at_64MB_plus"] = round(float((B[big] / T[big]).min()) / 1e9 / peak, 4)
+            res[mode + "_max_GBs"] = round(float((B / T).max()) / 1e9, 1)
+        streaming[op] = res
+    del pools
+    torch.cuda.empty_cache()
+
+    def mesh_case(N, K, rotate):
+        m = synth.Mesh(K, N, seed=1)
+        Z = bs.Map(m.E, N, m.NG, m.ids)
+        b_sc = 12 * m.NL + 8 * m.NG
+        b_ga = 12 * m.NL + 12 * m.NG + 4
+        reps = 1
+        if rotate:
+            reps = max(1, min(runs, -(-(512 << 20) // (8 * (m.NL + m.NG)))))
+        qGs = [torch.from_numpy(synth.uniform(m.NG, 2, 0)).cuda() for _ in range(1)]
+        qGs += [qGs[0].clone() for _ in range(reps - 1)]
+        qLs = [torch.empty(m.NL, dtype=torch.float64, device="cuda") for _ in range(reps)]
+        Z.scatter(qGs[0], qLs[0])
+        for q in qLs[1:]:
+            q.copy_(qLs[0])
+        outs = [torch.empty(m.NG, dtype=torch.float64, device="cuda") for _ in range(reps)]
+        t_sc = _sweep_time(lambda k: Z.scatter(qGs[k % reps], qLs[k % reps]), runs, flush)
+        t_ga = _sweep_time(lambda k: Z.gather(qLs[k % reps], outs[k % reps]), runs, flush)
+        out = {"N": N, "K": K, "N_L": m.NL, "N_G": m.NG, "scatter_bytes": b_sc,
+               "gather_bytes": b_ga, "scatter_s": t_sc, "gather_s": t_ga,
+               "scatter_GBs": round(b_sc / t_sc / 1e9, 1), "gather_GBs": round(b_ga / t_ga / 1e9, 1),
+               "scatter_frac": round(b_sc / t_sc / 1e9 / peak, 4),
+               "gather_frac": round(b_ga / t_ga / 1e9 / peak, 4)}
+        del Z, qGs, qLs, outs
+        torch.cuda.empty_cache()
+        return out
+
+    degree = [mesh_case(N, max(1, int(round((8e7) ** (1 / 3) / (N + 1)))), False)
+              for N in range(1, 16)]
+    ksweep = [mesh_case(7, K, True) for K in (2, 3, 4, 6, 8, 11, 16, 22, 30, 40, 48, 54)]
+    fits = {}
+    for op in ("scatter", "gather"):
+        B = np.array([c[op + "_bytes"] for c in ksweep], dtype=np.float64)
+        T = np.array([c[op + "_s"] for c in ksweep], dtype=np.float64)
+        t0, w = perfmodel.fit(B, T)
+        fits[op] = {"T0_us": round(t0 * 1e6, 3), "Wmax_GBs": round(w / 1e9, 1),
+                    "Wmax_frac": round(w / 1e9 / peak, 4),
+                    "B08_MiB": round(perfmodel.fischer_brown(t0, w) / 2 ** 20, 2)}
+    return {"peak_GBs": peak, "peak_kind": peak_kind, "runs_per_size": runs,
+            "timing": "CUDA graph of back-to-back C-ABI calls, best of 3 replays, L2 flushed "
+                      "before each replay",
+            "sizes": len(ns), "streaming": streaming,
+            "gather_scatter_by_degree_8e7_local_nodes": degree,
+            "gather_scatter_N7_K_sweep": ksweep, "gather_scatter_N7_fit": fits}
+
+
 def run_cg_only(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -668,64 +826,110 @@ def traffic_for(kernel, op):
 
 # ---------------------------------------------------------------- oracle on the host
 
-def oracle_sample(seconds=10.0):
-    """Time the oracle on a bounded sample of the same workload: BS1-BS5 at
-    n = 2^22, BS6/BS7 on the degree-7, 16^3 mesh.  Returns (GB/s, detail)."""
+def oracle_ops(host, mesh, omp=None):
+    """The seven operations of the step as oracle calls on the host inputs
+    at the benchmark's own sizes, in the step's order: [(op, call, bytes)].
+    omp: an oracle.Omp (the plain loops over all host cores) instead of the
+    single-threaded oracle."""
+    import numpy as np
+
     import oracle
-    from paper_2009_10917_gb300 import synth
-    n = 1 << 22
-    x, p, Ap, xc, r = (synth.uniform(n, 1, s) for s in range(5))
-    mesh = synth.Mesh(16, 7, seed=1)
-    qG = synth.uniform(mesh.NG, 2)
+    n = host["x"].size
     B = alg_bytes(n, mesh.NL, mesh.NG)
-    oracle.lib()
-    reps, t = 0, 0.0
-    while t < seconds or reps < 1:
+    st = {"y": np.empty(n), "qL": np.zeros(mesh.NL), "qG2": np.empty(mesh.NG)}
+    xc, r = host["xc"].copy(), host["r"].copy()
+    if omp is None:
+        calls = {
+            "copy": lambda: st.__setitem__("y", oracle.copy(host["x"])),
+            "axpy": lambda: st.__setitem__("y", oracle.axpy(0.5, host["x"], 1.0, st["y"])),
+            "norm": lambda: oracle.norm(host["x"]),
+            "dot": lambda: oracle.dot(host["x"], st["y"]),
+            "cg_update": lambda: oracle.cg_update(0.5, host["p"], host["Ap"], xc, r),
+            "scatter": lambda: st.__setitem__("qL", oracle.scatter(mesh.ids, host["qG"], st["qL"])),
+            "gather": lambda: oracle.gather(mesh.ids, st["qL"], mesh.NG)}
+    else:
+        rs, ci = oracle.csr(mesh.ids, mesh.NG)  # set-up of the CSR gather, not timed
+        calls = {
+            "copy": lambda: omp.copy(host["x"], st["y"]),
+            "axpy": lambda: omp.axpy(0.5, host["x"], 1.0, st["y"]),
+            "norm": lambda: omp.norm(host["x"]),
+            "dot": lambda: omp.dot(host["x"], st["y"]),
+            "cg_update": lambda: omp.cg_update(0.5, host["p"], host["Ap"], xc, r),
+            "scatter": lambda: omp.scatter(mesh.ids, host["qG"], st["qL"]),
+            "gather": lambda: omp.gather(rs, ci, st["qL"], st["qG2"])}
+    return [(op, calls[op], B[op]) for op in OPS]
+
+
+def time_oracle_pass(ops):
+    """One pass over the ops: (GB/s, seconds, per-op seconds)."""
+    per, tot, byt = {}, 0.0, 0
+    for op, call, b in ops:
         t0 = time.perf_counter()
-        y = oracle.copy(x)
-        y = oracle.axpy(0.5, x, 1.0, y)
-        oracle.norm(x)
-        oracle.dot(x, y)
-        xc, r, _ = oracle.cg_update(0.5, p, Ap, xc, r)
-        qL = oracle.scatter(mesh.ids, qG, __import__("numpy").zeros(mesh.NL))
-        oracle.gather(mesh.ids, qL, mesh.NG)
-        t += time.perf_counter() - t0
-        reps += 1
-    gbs = sum(B.values()) * reps / t / 1e9
-    return gbs, {"reps": reps, "seconds": round(t, 2),
-                 "sample": f"BS1-BS5 at n=2^22, BS6/BS7 on N=7 16^3 mesh, {reps} passes"}
+        call()
+        per[op] = time.perf_counter() - t0
+        tot += per[op]
+        byt += b
+    return byt / tot / 1e9, tot, per
 
 
-def cpu_baseline(args):
-    gbs, d = oracle_sample()
-    return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": d["sample"]}
+def cpu_baseline(args, host, mesh):
+    """The oracle on the host cores at the benchmark's own sizes (one full
+    pass of the step, inputs already in memory): single-threaded as it
+    stands, and the OpenMP build of its plain loops on every core."""
+    import oracle
+    oracle.lib()
+    gbs, secs, per = time_oracle_pass(oracle_ops(host, mesh))
+    sample = (f"one pass of BS1-BS7 at the benchmark's sizes (n=2^{args.log2n}; N={mesh.N} "
+              f"on {mesh.K}^3), inputs in host memory")
+    out = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": sample, "seconds": round(secs, 2),
+           "per_op_seconds": {k: round(v, 3) for k, v in per.items()}}
+    try:
+        om = oracle.Omp()
+        time_oracle_pass(oracle_ops(host, mesh, om))  # first touch of the work arrays
+        g2, s2, per2 = time_oracle_pass(oracle_ops(host, mesh, om))
+        out["omp"] = {"value": round(g2, 3), "unit": "GB/s", "cores": om.threads,
+                      "nproc": os.cpu_count(), "kind": "oracle loops, OpenMP",
+                      "sample": sample, "seconds": round(s2, 2),
+                      "per_op_seconds": {k: round(v, 3) for k, v in per2.items()}}
+    except Exception as exc:  # no OpenMP runtime on this host
+        out["omp"] = {"unavailable": str(exc)[:200]}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper's definitions as written),
+    single-threaded on the host, at the benchmark's own sizes.  Each step is
+    one operation of the step at full size, in the step's order, so K steps
+    cover K/7 passes; value = algorithmic bytes of the timed steps over their
+    time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n = 1 << args.log2n
-    N, K = (int(v) for v in args.mesh.split(","))
-    NL, NG = K ** 3 * (N + 1) ** 3, (K * N + 1) ** 3
-    for _ in range(max(0, min(args.warmup, 1))):
-        oracle_sample(1.0)
-    vals, t_all = [], 0.0
-    for _ in range(args.steps):
+    import oracle
+    oracle.lib()
+    n, mesh, host = make_inputs(args)
+    ops = oracle_ops(host, mesh)
+    for k in range(args.warmup):
+        ops[k % len(ops)][1]()
+    t_all, byt = 0.0, 0
+    for k in range(args.steps):
+        op, call, b = ops[(args.warmup + k) % len(ops)]
         t0 = time.perf_counter()
-        gbs, d = oracle_sample(2.0)
+        call()
         t_all += time.perf_counter() - t0
-        vals.append(gbs)
-    value = statistics.median(vals)
+        byt += b
+    value = byt / max(t_all, 1e-12) / 1e9
+    sample = (f"{args.steps} steps, one operation of the step each, at the benchmark's "
+              f"sizes (n=2^{args.log2n}; N={mesh.N} on {mesh.K}^3)")
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000 * t_all / max(1, args.steps), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": config(args, n, N, K, NL, NG),
+            "config": config(args, n, mesh.N, mesh.K, mesh.NL, mesh.NG),
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1,
-                             "kind": "oracle", "sample": d["sample"]},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -737,6 +941,14 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "cg":
         run_cg_only(a)
+    elif a.workload == "sweep":
+        res = sweep_section(a)
+        line = {"metric": "per-op HBM GB/s over sizes; T0/Wmax fit (Sec. 4, Table 2)",
+                "unit": "GB/s", "higher_is_better": True, "sweep": res}
+        if a.sweep_out:
+            with open(a.sweep_out, "w") as f:
+                json.dump(line, f, indent=1)
+        print(json.dumps(line), flush=True)
     elif a.workload == "batched":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

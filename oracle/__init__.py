@@ -8,6 +8,8 @@ and this directory imports nothing from the GPU package.
 ``bs_oracle.c`` holds the definitions (Table 1 BS1-BS7, eq. scatter_def,
 eqs. global_system / assembled_stiff / assembled_mass, Algorithm 1); this
 module only compiles it with gcc and marshals numpy arrays through ctypes.
+``bs_oracle_omp.c`` spreads the same plain BS loops over the host cores
+(OpenMP), only to time a multi-core CPU baseline (``Omp``).
 
 Parity is pinned for every routine here by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force and exact rational arithmetic).
@@ -42,6 +44,26 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+_OMP_LIB_PATH = os.path.join(_BUILD, "libbs_oracle_omp.so")
+_omp_lib = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile bs_oracle_omp.c (the plain BS loops over the host cores) with
+    gcc -fopenmp, same floating-point flags as the oracle."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_HERE, "bs_oracle_omp.c")
+    if not force and os.path.exists(_OMP_LIB_PATH) and \
+            os.path.getmtime(_OMP_LIB_PATH) >= os.path.getmtime(src):
+        return _OMP_LIB_PATH
+    tmp = _OMP_LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _OMP_LIB_PATH)
+    return _OMP_LIB_PATH
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -100,6 +122,60 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def omp_lib():
+    """Build (if stale) and load the OpenMP build of the plain BS loops."""
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            L = ctypes.CDLL(build_omp())
+            sigs = {"bso_omp_threads": (_int, []),
+                    "bso_omp_copy": (None, [_i64, _D, _D]),
+                    "bso_omp_axpy": (None, [_i64, _dbl, _D, _dbl, _D]),
+                    "bso_omp_norm": (None, [_i64, _D, _D]),
+                    "bso_omp_dot": (_dbl, [_i64, _D, _D]),
+                    "bso_omp_cg_update": (_dbl, [_i64, _dbl, _D, _D, _D, _D]),
+                    "bso_omp_scatter": (None, [_i64, _I, _D, _D]),
+                    "bso_omp_gather_csr": (None, [_i64, _I, _I, _D, _D])}
+            for name, (res, args) in sigs.items():
+                fn = getattr(L, name)
+                fn.restype, fn.argtypes = res, args
+            _omp_lib = L
+    return _omp_lib
+
+
+class Omp:
+    """The plain BS1-BS7 loops over all host cores (bs_oracle_omp.c); in
+    place on the caller's arrays, for timing.  gather() needs the CSR of
+    Z^T, built once from the map (csr())."""
+
+    def __init__(self):
+        self.L = omp_lib()
+        self.threads = self.L.bso_omp_threads()
+
+    def copy(self, x, y):
+        self.L.bso_omp_copy(x.size, _d(x), _d(y))
+
+    def axpy(self, alpha, x, beta, y):
+        self.L.bso_omp_axpy(x.size, alpha, _d(x), beta, _d(y))
+
+    def norm(self, x):
+        out = np.empty(2)
+        self.L.bso_omp_norm(x.size, _d(x), _d(out))
+        return out
+
+    def dot(self, x, y):
+        return self.L.bso_omp_dot(x.size, _d(x), _d(y))
+
+    def cg_update(self, alpha, p, Ap, x, r):
+        return self.L.bso_omp_cg_update(x.size, alpha, _d(p), _d(Ap), _d(x), _d(r))
+
+    def scatter(self, ids, qG, qL):
+        self.L.bso_omp_scatter(ids.size, _i(ids), _d(qG), _d(qL))
+
+    def gather(self, row_starts, col_ids, qL, qG):
+        self.L.bso_omp_gather_csr(qG.size, _i(row_starts), _i(col_ids), _d(qL), _d(qG))
 
 
 def _d(a):

@@ -25,9 +25,9 @@ def test_algorithmic_bytes_at_the_benchmark_sizes():
 
 
 def test_reference_arm_prints_the_contract_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], cwd=ROOT, capture_output=True, text=True,
-                         timeout=600)
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "8",
+                          "--warmup", "1", "--log2n", "18", "--mesh", "3,6"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -40,4 +40,5 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
-    assert d["config"]["workload"]
+    assert d["config"]["workload"] and d["config"]["n"] == 1 << 18
+    assert "n=2^18" in d["cpu_baseline"]["sample"]

@@ -838,3 +838,42 @@ def test_batched_workload_specs():
     Ns, Ks = zip(*specs)
     assert set(Ns) == set(range(2, 9)) and set(Ks) <= set(range(4, 25)) and len(set(Ks)) >= 18
     assert sum((k * n + 1) ** 3 for n, k in specs) == 157354317
+
+
+# ------------------------------------------------------------------ OpenMP build of the BS loops
+
+def test_omp_loops_match_the_single_threaded_oracle():
+    """The multi-core timing build (bs_oracle_omp.c) computes what the oracle
+    does: bitwise for the element-wise loops and the gather (same per-row
+    order), within an ulp or two of the single-threaded Dot2 for the
+    reductions (both are within about an ulp of the exact sum)."""
+    om = oracle.Omp()
+    n = 1_000_003
+    x, y, p, Ap, xc, r = (synth.uniform(n, 61, s) for s in range(6))
+    yy = np.empty(n)
+    om.copy(x, yy)
+    assert np.array_equal(yy, oracle.copy(x))
+    y2 = y.copy()
+    om.axpy(-1.3, x, 0.7, y2)
+    assert np.array_equal(y2, oracle.axpy(-1.3, x, 0.7, y))
+    s, sq = oracle.norm(x)
+    o = om.norm(x)
+    assert abs(o[0] - s) <= 4e-16 * s and abs(o[1] - sq) <= 4e-16 * sq
+    d = oracle.dot(x, y)
+    assert abs(om.dot(x, y) - d) <= 1e-15 * abs(d)
+    xw, rw = xc.copy(), r.copy()
+    rr = om.cg_update(0.37, p, Ap, xw, rw)
+    xo, ro, rro = oracle.cg_update(0.37, p, Ap, xc, r)
+    assert np.array_equal(xw, xo) and np.array_equal(rw, ro) and abs(rr - rro) <= 4e-16 * rro
+    m = synth.Mesh(6, 5, seed=2)
+    ids = _masked_ids(m, 0.05)
+    qG = synth.uniform(m.NG, 62)
+    qL = np.full(m.NL, -2.0)
+    om.scatter(ids, qG, qL)
+    assert np.array_equal(qL, oracle.scatter(ids, qG, np.full(m.NL, -2.0)))
+    ql = synth.uniform(m.NL, 63)
+    ql[::7] = -0.0
+    rs, ci = oracle.csr(ids, m.NG)
+    g = np.full(m.NG, np.nan)
+    om.gather(rs, ci, ql, g)
+    assert np.array_equal(g.view(np.uint64), oracle.gather(ids, ql, m.NG).view(np.uint64))
