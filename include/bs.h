@@ -224,8 +224,12 @@ int bs_diag_A(const bs_problem *prob, double *d_diag, void *stream);
  * node is FP64.  Error per node: a few units of 2^-46 times sum |K| |u|
  * (about 64 times the FP64 operator's); inputs below 2^-102 in magnitude
  * count as zero (scale b so that the entries that matter lie above that)
- * and inputs of 2^127 or more become infinite.  The gather is the same as
- * bs_apply_A's. */
+ * and inputs of 2^127 or more become infinite.  On a problem with geometric
+ * factors the six entries of w det J J^-1 J^-T and lambda w det J are split
+ * the same way, so the same window applies to them: they scale as L and
+ * lambda L^3 with the mesh's length scale L, and below 2^-102 they count as
+ * zero -- keep L above about 2^-28 (lambda of order 1) for the accuracy
+ * stated here.  The gather is the same as bs_apply_A's. */
 int bs_apply_A_ff(const bs_problem *prob, const double *p, double *Ap, void *stream);
 
 /* How A p is formed, process-wide, by bs_apply_A, bs_apply_local,
@@ -262,7 +266,8 @@ enum {
   BS_CG_X0 = 8,          /* x holds the initial guess (else x0 = 0)        */
   BS_CG_REFINED_F32 = 32, /* batched: FP32 inner CG, FP64 refinement       */
   BS_CG_FF_OPERATOR = 256, /* the float-float operator of bs_apply_A_ff     */
-  BS_CG_SCATTERED = 512     /* bs_cg_solve: vectors in scattered storage    */
+  BS_CG_SCATTERED = 512,    /* bs_cg_solve: vectors in scattered storage    */
+  BS_CG_BLOCK_JACOBI = 1024 /* bs_cg_solve: element-interior block Jacobi   */
 };
 
 typedef struct {
@@ -293,7 +298,15 @@ typedef struct {
  * global node, the lowest local index, so that it equals the global one
  * term for term; b and x stay N_G vectors at the boundary; 122 N_L + 20 N_G
  * bytes per iteration against 24 N_L + 100 N_G in global storage, 1.5 times
- * as many at N = 7).  Synchronises
+ * as many at N = 7), BS_CG_BLOCK_JACOBI (the preconditioned Algorithm 1
+ * with z = D^-1 r except on element interiors, where z_I = A_II^-1 r_I
+ * solves the interior block of the element matrix exactly -- on every
+ * element whose interior nodes are unmasked and held by that element alone;
+ * no counterpart in the paper: it is the exact form of the map the learned
+ * preconditioner imitates.  A_II^-1 is applied by fast diagonalisation, the
+ * 1-D generalised eigenvectors of the interior stiffness and mass blocks, in
+ * FP32 on per-element power-of-two-normalised values; affine elements of
+ * degree 2..9 in global storage only).  Synchronises
  * `stream` before returning; info (host) may be NULL.  Returns
  * BS_ERR_NOT_CONVERGED if maxit is reached without BS_CG_FIXED_ITERS,
  * BS_ERR_BREAKDOWN on p.Ap <= 0. */
@@ -447,6 +460,18 @@ int bs_mlp_destroy(bs_mlp *mlp);
 /* Copy the FP32 master weights to HOST h_W1 [H x D], h_W2 [D x H] (either
  * may be NULL).  Synchronous. */
 int bs_mlp_get_weights(const bs_mlp *mlp, float *h_W1, float *h_W2);
+/* Checkpointing the training state (the paper has no learned part; this is
+ * the library's own): the FP32 master weights, both layers' Adam moments and
+ * the Adam step count, as one host image of bs_mlp_state_bytes() bytes (a
+ * header with the shape and the step, then the device arrays as stored).
+ * Loading it into a network of the same D, H and precision mode and training
+ * on continues bitwise as if training had never stopped.  Both calls
+ * synchronise the device.  Errors: BS_ERR_ARG (short buffer, not an image,
+ * shape or mode mismatch), BS_ERR_CUDA.  bs_mlp_state_bytes returns -1 for a
+ * NULL network. */
+int64_t bs_mlp_state_bytes(const bs_mlp *mlp);
+int bs_mlp_save_state(const bs_mlp *mlp, void *h_buf, int64_t nbytes);
+int bs_mlp_load_state(bs_mlp *mlp, const void *h_buf, int64_t nbytes);
 /* d_Y [B x D] = f(d_X [B x D]) (DEVICE float), or the odd part with
  * BS_MLP_ODD.  Scratch for B rows is allocated on first use and kept. */
 int bs_mlp_forward(bs_mlp *mlp, int64_t B, const float *d_X, float *d_Y,

@@ -95,6 +95,8 @@ _SIGS = {
     "bso_cg": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int, _int,
                       _D, _D, _D]),
     "bso_pcg_jacobi": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int, _D]),
+    "bso_pcg_block_jacobi": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _D, _dbl, _int,
+                                    _D]),
     "bso_apply_A_geo": (_int, [_int, _int, _dbl, _D, _D, _I, _i64, _D, _D]),
     "bso_apply_local_geo": (_int, [_int, _int, _dbl, _D, _D, _D, _D]),
     "bso_diag_A_geo": (_int, [_int, _int, _dbl, _D, _D, _I, _i64, _D]),
@@ -387,6 +389,19 @@ def pcg_jacobi(E, N, h, lam, ids, NG, b, tol=1e-8, maxit=1000, coef=None):
 # trilinear map of bs_oracle.c); the operator is the same weak form with the
 # non-affine geometric factors w det J J^-1 J^-T at every GLL node.
 
+def pcg_block_jacobi(E, N, h, lam, ids, NG, b, tol=1e-8, maxit=1000, coef=None):
+    """PCG with the element-interior blocks solved exactly (Cholesky) and
+    Jacobi elsewhere.  Returns (x, iters, rr[])."""
+    ids, b, coef = _ids(ids), _f64(b), _coef(coef)
+    x = np.zeros(int(NG))
+    hr = np.zeros(maxit + 1)
+    it = lib().bso_pcg_block_jacobi(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG),
+                                    _d(b), _d(x), float(tol), int(maxit), _d(hr))
+    if it < 0:
+        raise RuntimeError(f"bso_pcg_block_jacobi failed ({it})")
+    return x, it, hr[:it + 1]
+
+
 def _verts(verts, E):
     v = np.ascontiguousarray(verts, dtype=np.float64)
     if v.size != 24 * E:
@@ -474,13 +489,16 @@ _SIGS.update({
                         _dbl, _int, _D, ctypes.POINTER(_int)]),
     "bso_interior_pairs": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _D, _i64, _I, _int, _F,
                                   _F]),
+    "bso_fpcg_judged": (_int, [_int, _int, _dbl, _dbl, _D, _I, _i64, _F, _F, _int, _int, _int,
+                               _D, _D, _dbl, _int, _int, _int, _D, ctypes.POINTER(_int),
+                               ctypes.POINTER(_int)]),
 })
 
 
 def _lib_mlp():
     L = lib()
     for name in ("bso_bf16_round", "bso_mlp_forward", "bso_mlp_loss_grad", "bso_adam", "bso_fpcg",
-                 "bso_interior_pairs"):
+                 "bso_interior_pairs", "bso_fpcg_judged"):
         res, args = _SIGS[name]
         fn = getattr(L, name)
         fn.restype, fn.argtypes = res, args
@@ -546,6 +564,32 @@ def fpcg(E, N, h, lam, ids, NG, b, W1=None, W2=None, prec=PREC_BF16, odd=False, 
     if it < 0:
         raise RuntimeError(f"bso_fpcg failed ({it})")
     return x, it, hr[:it + 1], fb.value
+
+
+def judge_stall(NG):
+    """The Jacobi judge's patience: max(1024, 16 N_G^(1/3)) iterations."""
+    return max(1024, int(16.0 * float(NG) ** (1.0 / 3.0)))
+
+
+def fpcg_judged(E, N, h, lam, ids, NG, b, W1, W2, prec=PREC_BF16, odd=False, tol=1e-8,
+                maxit=10000, coef=None, period=8, stall=None):
+    """Flexible PCG with the learned correction and the Jacobi judge checked
+    every `period` iterations (patience `stall`, default judge_stall(NG)).
+    Returns (x, iters, rr[], fallbacks, switched_at)."""
+    ids, b, coef = _ids(ids), _f64(b), _coef(coef)
+    x = np.zeros(int(NG))
+    hr = np.zeros(maxit + 2)
+    fb, sw = ctypes.c_int(0), ctypes.c_int(0)
+    W1p, W2p = _f32(W1), _f32(W2)
+    stall = judge_stall(NG) if stall is None else int(stall)
+    it = _lib_mlp().bso_fpcg_judged(E, N, float(h), float(lam), _d(coef), _i(ids), int(NG),
+                                    _fp(W1p), _fp(W2p), int(W1p.shape[0]), int(prec),
+                                    int(bool(odd)), _d(b), _d(x), float(tol), int(maxit),
+                                    int(period), stall, _d(hr), ctypes.byref(fb),
+                                    ctypes.byref(sw))
+    if it < 0:
+        raise RuntimeError(f"bso_fpcg_judged failed ({it})")
+    return x, it, hr[:it + 1], fb.value, sw.value
 
 
 def interior_pairs(E, N, h, lam, ids, NG, r, elems, negate_odd=False, coef=None):

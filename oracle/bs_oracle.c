@@ -680,6 +680,121 @@ int bso_pcg_jacobi_geo(int E, int N, double lambda, const double *coef, const do
 }
 
 /* ------------------------------------------------------------------------ */
+/* Block-Jacobi PCG (the exact form of the learned preconditioner's map):   */
+/* z = M^-1 r with, for every element e whose interior local nodes I_e are  */
+/* all unmasked and held by e alone (valence 1), the block solved exactly,  */
+/*   z[ids(I_e)] = A_II^-1 r[ids(I_e)],  A_II = rows/cols I_e of            */
+/*   c_e S_e + lambda M_e (Cholesky, factored once per element),            */
+/* and z_g = r_g / diag(A)_g at every other node.  Algorithm 1 with z.      */
+/* ------------------------------------------------------------------------ */
+int bso_pcg_block_jacobi(int E, int N, double h, double lambda, const double *coef,
+                         const int32_t *ids, int64_t NG, const double *b, double *x,
+                         double tol, int maxit, double *hist_rr) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq, nImax = (N - 1) * (N - 1) * (N - 1);
+  double gr[33], gw[33], gD[33 * 33];
+  if (N < 2 || bso_gll(N, gr, gw, gD)) return -3;
+  bso_problem P = {E, N, h, lambda, coef, ids, NG, NULL};
+  double *vec = malloc(sizeof(double) * 5 * (NG > 0 ? NG : 1));
+  double *L = malloc(sizeof(double) * (size_t)E * nImax * nImax + 1);
+  int *I = malloc(sizeof(int) * (size_t)E * nImax + 1), *nI = malloc(sizeof(int) * (E + 1));
+  int *val = malloc(sizeof(int) * (NG > 0 ? NG : 1));
+  double *tmp = malloc(sizeof(double) * 6 * Np);
+  if (!vec || !L || !I || !nI || !val || !tmp) {
+    free(vec); free(L); free(I); free(nI); free(val); free(tmp);
+    return -2;
+  }
+  double *r = vec, *p = r + NG, *Ap = p + NG, *z = Ap + NG, *dg = z + NG;
+  double *unit = tmp, *col = unit + Np, *t1 = col + Np, *t2 = t1 + Np, *t3 = t2 + Np,
+         *y = t3 + Np;
+  bso_diag_A(E, N, h, lambda, coef, ids, NG, dg);
+  bso_valence((int64_t)E * Np, NG, ids, val);
+  int rc = 0;
+  for (int e = 0; e < E && !rc; ++e) {
+    const int32_t *id = ids + (int64_t)e * Np;
+    int *Ie = I + (size_t)e * nImax;
+    double *Le = L + (size_t)e * nImax * nImax;
+    int n = 0, all = 1;
+    for (int k = 1; k < N; ++k)
+      for (int j = 1; j < N; ++j)
+        for (int i = 1; i < N; ++i) {
+          const int l = i + Nq * (j + Nq * k);
+          if (id[l] >= 0 && val[id[l]] == 1)
+            Ie[n++] = l;
+          else
+            all = 0;
+        }
+    if (!all) n = 0;  /* the interior is not a block of A: Jacobi there */
+    nI[e] = n;
+    for (int c = 0; c < n; ++c) {  /* column c of A_II */
+      for (int l = 0; l < Np; ++l) unit[l] = 0.0;
+      unit[Ie[c]] = 1.0;
+      element_apply(&P, gr, gw, gD, e, unit, col, t1, t2, t3);
+      for (int a = 0; a < n; ++a) Le[a * n + c] = col[Ie[a]];
+    }
+    for (int c = 0; c < n && !rc; ++c) {  /* A_II = L L^T */
+      double d = Le[c * n + c];
+      for (int k = 0; k < c; ++k) d -= Le[c * n + k] * Le[c * n + k];
+      if (!(d > 0.0)) { rc = -4; break; }
+      d = sqrt(d);
+      Le[c * n + c] = d;
+      for (int a = c + 1; a < n; ++a) {
+        double v = Le[a * n + c];
+        for (int k = 0; k < c; ++k) v -= Le[a * n + k] * Le[c * n + k];
+        Le[a * n + c] = v / d;
+      }
+    }
+  }
+  /* z = M^-1 r */
+#define BJ_APPLY()                                                          \
+  do {                                                                      \
+    for (int64_t g = 0; g < NG; ++g) z[g] = r[g] / dg[g];                   \
+    for (int e = 0; e < E; ++e) {                                           \
+      const int32_t *id = ids + (int64_t)e * Np;                            \
+      const int *Ie = I + (size_t)e * nImax, n = nI[e];                     \
+      const double *Le = L + (size_t)e * nImax * nImax;                     \
+      for (int a = 0; a < n; ++a) {                                         \
+        double v = r[id[Ie[a]]];                                            \
+        for (int k = 0; k < a; ++k) v -= Le[a * n + k] * y[k];              \
+        y[a] = v / Le[a * n + a];                                           \
+      }                                                                     \
+      for (int a = n - 1; a >= 0; --a) {                                    \
+        double v = y[a];                                                    \
+        for (int k = a + 1; k < n; ++k) v -= Le[k * n + a] * y[k];          \
+        y[a] = v / Le[a * n + a];                                           \
+      }                                                                     \
+      for (int a = 0; a < n; ++a) z[id[Ie[a]]] = y[a];                      \
+    }                                                                       \
+  } while (0)
+  int j = 0;
+  if (!rc) {
+    apply_A(&P, x, Ap);
+    for (int64_t g = 0; g < NG; ++g) r[g] = b[g] - Ap[g];
+    BJ_APPLY();
+    for (int64_t g = 0; g < NG; ++g) p[g] = z[g];
+    double rz = dot2(NG, r, z), rr = dot2(NG, r, r);
+    const double eps = tol * tol * dot2(NG, b, b);
+    if (hist_rr) hist_rr[0] = rr;
+    while (j < maxit && rr > eps) {
+      apply_A(&P, p, Ap);
+      const double pAp = dot2(NG, p, Ap);
+      if (!(pAp > 0.0) || !isfinite(pAp)) { rc = -1; break; }
+      const double alpha = rz / pAp;
+      rr = bso_cg_update(NG, alpha, p, Ap, x, r);
+      BJ_APPLY();
+      const double rz_new = dot2(NG, r, z);
+      const double beta = rz_new / rz;
+      for (int64_t g = 0; g < NG; ++g) p[g] = fma(1.0, z[g], beta * p[g]);
+      rz = rz_new;
+      ++j;
+      if (hist_rr) hist_rr[j] = rr;
+    }
+  }
+#undef BJ_APPLY
+  free(vec); free(L); free(I); free(nI); free(val); free(tmp);
+  return rc ? rc : j;
+}
+
+/* ------------------------------------------------------------------------ */
 /* FP32-storage CG inside an FP64 iterative-refinement loop.                */
 /* Outer (FP64): r = b - A x; stop when ||r|| <= outer_tol ||b||; solve     */
 /* A d = r approximately in FP32; x = x + d.                                */

@@ -215,11 +215,19 @@ static double dot(int64_t n, const double *a, const double *b) {
 }
 
 /* Flexible PCG; returns iterations (or -1 breakdown, -2 alloc); *fallbacks
- * counts iterations whose correction was rejected. */
-int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const int32_t *ids,
-             int64_t NG, const float *W1, const float *W2, int H, int prec, int odd,
-             const double *b, double *x, double tol, int maxit, double *hist_rr,
-             int *fallbacks) {
+ * counts iterations whose correction was rejected.
+ *
+ * The Jacobi judge (period > 0): after every `period`-th iteration the
+ * residual is compared with the last one that marked progress; when r.r has
+ * dropped to a quarter of it (the residual norm halved) this iterate marks
+ * progress, otherwise once `stall` iterations have passed since the last
+ * progress the learned correction is dropped for good and the iteration
+ * restarts from the current x with the Jacobi preconditioner: z = D^-1 r,
+ * p = z.  *switched_at receives that iteration (0: never). */
+int bso_fpcg_judged(int E, int N, double h, double lambda, const double *coef,
+                    const int32_t *ids, int64_t NG, const float *W1, const float *W2, int H,
+                    int prec, int odd, const double *b, double *x, double tol, int maxit,
+                    int period, int stall, double *hist_rr, int *fallbacks, int *switched_at) {
   double *buf = malloc(sizeof(double) * 6 * NG);
   if (!buf) return -2;
   double *r = buf, *p = r + NG, *Ap = p + NG, *z = Ap + NG, *zn = z + NG, *dg = zn + NG;
@@ -239,6 +247,9 @@ int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const in
   const double eps = tol * tol * dot(NG, b, b);
   if (hist_rr) hist_rr[0] = rr;
   int j = 0;
+  double progress_rr = INFINITY;
+  int progress_it = 0;
+  if (switched_at) *switched_at = 0;
   while (j < maxit && rr > eps) {
     bso_apply_A(E, N, h, lambda, coef, ids, NG, p, Ap);
     const double pAp = dot(NG, p, Ap);
@@ -252,6 +263,22 @@ int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const in
     ++j;
     if (hist_rr) hist_rr[j] = rr;
     if (rr <= eps) break;
+    if (period > 0 && W2 && j % period == 0) {
+      if (rr <= 0.25 * progress_rr) {
+        progress_rr = rr;
+        progress_it = j;
+      } else if (j - progress_it >= stall) {
+        W1 = NULL;  /* Jacobi from here on */
+        W2 = NULL;
+        if (switched_at) *switched_at = j;
+        for (int64_t g = 0; g < NG; ++g) {
+          z[g] = r[g] / dg[g];
+          p[g] = z[g];
+        }
+        rz = dot(NG, r, z);
+        continue;
+      }
+    }
     precond(E, N, ids, NG, dg, W1, W2, H, prec, odd, r, zn);
     double rzn = dot(NG, r, zn);
     if (!(rzn > 0.0) || !isfinite(rzn)) {
@@ -269,4 +296,12 @@ int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const in
   if (fallbacks) *fallbacks = fb;
   free(buf);
   return j;
+}
+
+int bso_fpcg(int E, int N, double h, double lambda, const double *coef, const int32_t *ids,
+             int64_t NG, const float *W1, const float *W2, int H, int prec, int odd,
+             const double *b, double *x, double tol, int maxit, double *hist_rr,
+             int *fallbacks) {
+  return bso_fpcg_judged(E, N, h, lambda, coef, ids, NG, W1, W2, H, prec, odd, b, x, tol, maxit,
+                         0, 0, hist_rr, fallbacks, NULL);
 }

@@ -35,6 +35,7 @@ BS_CG_X0 = 8
 BS_CG_REFINED_F32 = 32
 BS_CG_FF_OPERATOR = 256
 BS_CG_SCATTERED = 512
+BS_CG_BLOCK_JACOBI = 1024
 BS_OP_FUSED = 1
 BS_OP_DIRECT = 2
 BS_MLP_BF16X3 = 1
@@ -511,6 +512,9 @@ _SIGS.update({
     "bs_rows_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bs_set_wait_budget": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "bs_gemm_engine": (ctypes.c_int, [_i32]),
+    "bs_mlp_state_bytes": (ctypes.c_int64, [_vp]),
+    "bs_mlp_save_state": (ctypes.c_int, [_vp, _vp, _i64]),
+    "bs_mlp_load_state": (ctypes.c_int, [_vp, _vp, _i64]),
     "bs_mlp_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _pp]),
     "bs_mlp_destroy": (ctypes.c_int, [_vp]),
     "bs_mlp_get_weights": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -595,6 +599,30 @@ class MLP:
         _check(lib().bs_mlp_train_step(self.handle, X.shape[0], _fptr(X, "X"), _fptr(T, "T"),
                                        float(lr), _ptr(loss), _stream()), "bs_mlp_train_step")
         return loss
+
+    def save_state(self) -> bytes:
+        """The training state (masters, Adam moments, step) as a host image
+        (bs_mlp_save_state)."""
+        L = _bind(["bs_mlp_state_bytes", "bs_mlp_save_state"])
+        n = L.bs_mlp_state_bytes(self.handle)
+        buf = ctypes.create_string_buffer(n)
+        _check(L.bs_mlp_save_state(self.handle, buf, n), "bs_mlp_save_state")
+        return buf.raw
+
+    def load_state(self, image: bytes):
+        """Restore a training state saved from a network of the same shape
+        and mode (bs_mlp_load_state)."""
+        L = _bind(["bs_mlp_load_state"])
+        buf = ctypes.create_string_buffer(bytes(image), len(image))
+        _check(L.bs_mlp_load_state(self.handle, buf, len(image)), "bs_mlp_load_state")
+
+    def save(self, path):
+        with open(path, "wb") as f:
+            f.write(self.save_state())
+
+    def load(self, path):
+        with open(path, "rb") as f:
+            self.load_state(f.read())
 
 
 def mlp_pairs(problem, r, elems, negate_odd=False, out=None):

@@ -1,0 +1,262 @@
+// bs_bj.cuh -- the element-interior block-Jacobi preconditioner of
+// BS_CG_BLOCK_JACOBI: z = D^-1 r, except that on every element whose interior
+// nodes belong to it alone the interior block of the element matrix is
+// inverted exactly, z_I = A_II^-1 r_I.  This is the map the learned
+// preconditioner is trained to imitate (its targets are A_II^-1 r_I), in
+// closed form.
+//
+// On an affine cube A_II = c_e (h/2) (K x W x W + W x K x W + W x W x K)_II
+// + lambda (h/2)^3 (W x W x W)_II is a sum of Kronecker products of the 1-D
+// interior blocks K_ii and W_ii, so the generalized eigenvectors of
+// K_ii v = mu W_ii v (V^T W_ii V = I) diagonalise it (the fast diagonalisation
+// method of Lynch, Rice & Thomas, 1964):
+//   A_II^-1 = (V x V x V) diag(1 / (c_e (h/2)(mu_a + mu_b + mu_c) + lambda (h/2)^3))
+//             (V x V x V)^T,
+// i.e. three 1-D transforms, a diagonal scaling and three transforms back,
+// 6 (N-1) multiply-adds per interior node.  The transforms run in FP32 on
+// values normalised per element by a power of two (a preconditioner needs no
+// more precision, and the FP32 pipes are 64 times GB300's FP64 rate); the
+// result is scaled back exactly.
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+#include "bs_op.cuh"
+
+namespace bs {
+
+constexpr int kBjMaxNi = 8;  // interior points per direction: N <= 9
+
+struct BjTab {
+  float V[kBjMaxNi * kBjMaxNi];  // V[m * ni + a]: component m of eigenvector a
+  float mu[kBjMaxNi];
+};
+
+// Eigen-decomposition of a symmetric n x n matrix A (row-major, destroyed) by
+// cyclic Jacobi rotations: A = Q diag(lam) Q^T, Q[m * n + a] = component m of
+// eigenvector a.
+inline void sym_eig(int n, double *A, double *Q, double *lam) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Q[i * n + j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) /
+                         (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // A <- A J (columns p, q)
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // A <- J^T A (rows p, q)
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {  // Q <- Q J
+          const double qkp = Q[k * n + p], qkq = Q[k * n + q];
+          Q[k * n + p] = c * qkp - s * qkq;
+          Q[k * n + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+}
+
+// qual[e] = 1 when every interior node of element e is unmasked and has no
+// other copy (valence 1): only then is the element's interior block a
+// diagonal block of A.
+__global__ void k_bj_qualify(int64_t E, int N, const int32_t *__restrict__ ids,
+                             const int32_t *__restrict__ row_starts, uint8_t *__restrict__ qual) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += nth) {
+    uint8_t ok = 1;
+    for (int k = 1; k < N && ok; ++k)
+      for (int j = 1; j < N && ok; ++j)
+        for (int i = 1; i < N && ok; ++i) {
+          const int32_t g = ids[e * Np + i + Nq * (j + Nq * k)];
+          ok = g >= 0 && row_starts[g + 1] - row_starts[g] == 1;
+        }
+    qual[e] = ok;
+  }
+}
+
+// The preconditioner's interior part, after z = D^-1 r has been written
+// everywhere: z_I = A_II^-1 r_I on every qualifying element, and the r.z
+// correction sum r_I (z_I - D_I^-1 r_I).  The last block adds it to the
+// Jacobi part of r.z (held in st) and, except at init, forms beta and
+// advances the iteration.  EPB elements per block of 256 threads, one
+// thread per interior node (two when ni^3 > 256).
+template <int NI>
+__global__ void __launch_bounds__(256)
+    k_bj_apply(int64_t E, int N, const int32_t *__restrict__ ids, const uint8_t *__restrict__ qual,
+               const double *__restrict__ coef, float g, float mlam, const BjTab *__restrict__ tab,
+               const double *__restrict__ r, const double *__restrict__ dinv,
+               double *__restrict__ z, double *partials, unsigned int *counter, CgState *st,
+               int init) {
+  constexpr int NN = NI * NI * NI;
+  constexpr int EPB = NN >= 256 ? 1 : 256 / NN;
+  constexpr int PER = (NN + 255) / 256;
+  __shared__ float s_a[EPB * NN], s_b[EPB * NN];
+  __shared__ float s_V[NI * NI], s_mu[NI];
+  __shared__ int s_ex[EPB];
+  if (!init && cg_halted(st)) return;
+  for (int t = threadIdx.x; t < NI * NI; t += 256) s_V[t] = tab->V[t];
+  if (threadIdx.x < NI) s_mu[threadIdx.x] = tab->mu[threadIdx.x];
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  double acc = 0.0;
+  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < E; e0 += (int64_t)gridDim.x * EPB) {
+    int32_t gid[PER];
+    double rv[PER];
+    bool on[PER];
+    if (threadIdx.x < EPB) s_ex[threadIdx.x] = -2000;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int f = threadIdx.x + 256 * u, slot = f / NN, q = f - slot * NN;
+      const int64_t e = e0 + slot;
+      on[u] = f < EPB * NN && e < E && qual[e];
+      gid[u] = -1;
+      rv[u] = 0.0;
+      if (on[u]) {
+        const int a = q % NI, b = (q / NI) % NI, c = q / (NI * NI);
+        gid[u] = ids[e * Np + (a + 1) + Nq * ((b + 1) + Nq * (c + 1))];
+        rv[u] = r[gid[u]];
+        if (rv[u] != 0.0) atomicMax(&s_ex[slot], ilogb(rv[u]));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int f = threadIdx.x + 256 * u;
+      if (f < EPB * NN) s_a[f] = on[u] ? (float)ldexp(rv[u], -s_ex[f / NN]) : 0.f;
+    }
+    __syncthreads();
+    // (V x V x V)^T: along a, then b, then c (s_a -> s_b -> s_a -> s_b)
+#pragma unroll
+    for (int pass = 0; pass < 6; ++pass) {
+      const float *in = (pass & 1) ? s_b : s_a;
+      float *out = (pass & 1) ? s_a : s_b;
+      const int dim = pass % 3;
+      const bool fwd = pass < 3;
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int f = threadIdx.x + 256 * u;
+        if (f < EPB * NN) {
+          const int slot = f / NN, q = f - slot * NN;
+          const int a = q % NI, b = (q / NI) % NI, c = q / (NI * NI);
+          const int ix = dim == 0 ? a : (dim == 1 ? b : c);
+          const int stride = dim == 0 ? 1 : (dim == 1 ? NI : NI * NI);
+          const float *line = in + slot * NN + (q - ix * stride);
+          float s = 0.f;
+#pragma unroll
+          for (int m = 0; m < NI; ++m)
+            s = fmaf(fwd ? s_V[m * NI + ix] : s_V[ix * NI + m], line[m * stride], s);
+          if (pass == 2) {  // the diagonal scaling, between the two halves
+            const float ce = coef ? (float)coef[e0 + slot < E ? e0 + slot : 0] : 1.0f;
+            s = s / fmaf(ce * g, s_mu[a] + s_mu[b] + s_mu[c], mlam);
+          }
+          out[f] = s;
+        }
+      }
+      __syncthreads();
+    }
+    // after six passes the result is in s_a
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (!on[u]) continue;
+      const int f = threadIdx.x + 256 * u;
+      const double zv = ldexp((double)s_a[f], s_ex[f / NN]);
+      z[gid[u]] = zv;
+      acc = fma(rv[u], zv - dinv[gid[u]] * rv[u], acc);
+    }
+    __syncthreads();
+  }
+  const double part = block_sum<256>(acc);
+  double delta;
+  if (grid_combine<256>(part, partials, counter, &delta) && threadIdx.x == 0) {
+    if (init) {
+      st->rz = st->rz + delta;
+    } else {
+      const double rz = st->rz_next + delta;
+      const double beta = rz / st->rz;
+      st->rz = rz;
+      cg_advance(st, st->rr_next, beta);
+    }
+  }
+}
+
+// Device tables (V, mu) and per-element flags of a problem, built on first use.
+inline int bj_ensure(bs_problem *P, cudaStream_t s) {
+  if (P->d_bj) return BS_OK;
+  const int N = P->N, Nq = N + 1, ni = N - 1;
+  OpTab<double> tab;
+  BS_CUDA_TRY(cudaMemcpy(&tab, P->d_tab, sizeof(tab), cudaMemcpyDeviceToHost));
+  // B = W_ii^-1/2 K_ii W_ii^-1/2 = Q diag(mu) Q^T; V = W_ii^-1/2 Q
+  std::vector<double> B((size_t)ni * ni), Q((size_t)ni * ni), mu(ni);
+  for (int a = 0; a < ni; ++a)
+    for (int b = 0; b < ni; ++b)
+      B[(size_t)a * ni + b] = tab.K[(a + 1) * Nq + (b + 1)] /
+                              std::sqrt(tab.w[a + 1] * tab.w[b + 1]);
+  sym_eig(ni, B.data(), Q.data(), mu.data());
+  BjTab h{};
+  for (int m = 0; m < ni; ++m) {
+    for (int a = 0; a < ni; ++a)
+      h.V[m * ni + a] = (float)(Q[(size_t)m * ni + a] / std::sqrt(tab.w[m + 1]));
+    h.mu[m] = (float)mu[m];
+  }
+  const int64_t E = P->map->E;
+  void *mem = nullptr;
+  BS_CUDA_TRY(cudaMalloc(&mem, 512 + (size_t)(E > 0 ? E : 1)));
+  P->d_bj = mem;
+  BS_CUDA_TRY(cudaMemcpy(mem, &h, sizeof(h), cudaMemcpyHostToDevice));
+  uint8_t *qual = static_cast<uint8_t *>(mem) + 512;
+  if (E > 0) {
+    k_bj_qualify<<<stream_grid(E, 1, 256, 4), 256, 0, s>>>(E, N, P->map->d_ids,
+                                                           P->map->d_row_starts, qual);
+    BS_LAUNCH_CHECK();
+  }
+  return BS_OK;
+}
+
+// z_I = A_II^-1 r_I on the qualifying elements (z = D^-1 r already written).
+inline int bj_apply(const bs_problem *P, const double *r, const double *dinv, double *z,
+                    int init, cudaStream_t s) {
+  const int64_t E = P->map->E;
+  if (E == 0) return BS_OK;
+  const BjTab *tab = static_cast<const BjTab *>(P->d_bj);
+  const uint8_t *qual = static_cast<const uint8_t *>(P->d_bj) + 512;
+  const float g = (float)(0.5 * P->h), mlam = (float)(P->lambda * 0.125 * P->h * P->h * P->h);
+  auto launch = [&](auto kern, int nn) -> int {
+    const int epb = nn >= 256 ? 1 : 256 / nn;
+    int grid = stream_grid((E + epb - 1) / epb, 1, 1, blocks_per_sm(kern, 256));
+    if (grid > kMaxPartials) grid = kMaxPartials;
+    kern<<<grid, 256, 0, s>>>(E, P->N, P->map->d_ids, qual, P->d_coef, g, mlam, tab, r, dinv, z,
+                              P->d_partials, P->d_counter, P->d_state, init);
+    BS_LAUNCH_CHECK();
+    return BS_OK;
+  };
+  switch (P->N - 1) {
+    case 1: return launch(k_bj_apply<1>, 1);
+    case 2: return launch(k_bj_apply<2>, 8);
+    case 3: return launch(k_bj_apply<3>, 27);
+    case 4: return launch(k_bj_apply<4>, 64);
+    case 5: return launch(k_bj_apply<5>, 125);
+    case 6: return launch(k_bj_apply<6>, 216);
+    case 7: return launch(k_bj_apply<7>, 343);
+    case 8: return launch(k_bj_apply<8>, 512);
+    default: return fail(BS_ERR_ARG, "block Jacobi: degree %d outside 2..9", P->N);
+  }
+}
+
+}  // namespace bs

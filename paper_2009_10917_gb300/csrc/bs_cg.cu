@@ -26,6 +26,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "bs_bj.cuh"
 #include "bs_op_ff.cuh"
 
 namespace bs {
@@ -68,25 +69,6 @@ struct EpAlpha {  // pAp -> alpha = rr / pAp (rz / pAp when preconditioned)
   }
 };
 
-__device__ __forceinline__ void cg_advance(CgState *st, double rr_new, double beta) {
-  const int j = st->iter;
-  if (st->hist) {
-    st->hist[3 * j] = st->alpha;
-    st->hist[3 * j + 1] = beta;
-    st->hist[3 * j + 2] = rr_new;
-  }
-  st->beta = beta;
-  st->beta_f = (float)beta;
-  st->rr = rr_new;
-  st->iter = j + 1;
-  if (!isfinite(rr_new) || !isfinite(beta))
-    st->done = 2;
-  else if (!st->fixed && rr_new <= st->eps)
-    st->done = 1;
-  else if (j + 1 >= st->maxit)
-    st->done = 3;
-}
-
 struct EpBeta {  // rr' -> beta = rr'/rr (Algorithm 1, step 10)
   CgState *st;
   __device__ __forceinline__ void operator()(double s) const {
@@ -100,7 +82,7 @@ __global__ void __launch_bounds__(kReduceBlock)
     k_pcg_update(int64_t n, const double *__restrict__ p, const double *__restrict__ Ap,
                  const double *__restrict__ dinv, double *__restrict__ x,
                  double *__restrict__ r, double *__restrict__ z, double *partials,
-                 unsigned int *counter, CgState *st, int init) {
+                 unsigned int *counter, CgState *st, int init, int defer) {
   if (!init && cg_halted(st)) return;
   const double alpha = init ? 0.0 : st->alpha;
   const double nalpha = -alpha;
@@ -130,6 +112,9 @@ __global__ void __launch_bounds__(kReduceBlock)
       st->done = !(isfinite(trr) && isfinite(trz))
                      ? 2
                      : ((!st->fixed && trr <= st->eps) ? 1 : (st->maxit <= 0 ? 3 : 0));
+    } else if (defer) {  // block Jacobi completes z and r.z, then advances
+      st->rr_next = trr;
+      st->rz_next = trz;
     } else {
       const double beta = trz / st->rz;
       st->rz = trz;
@@ -169,14 +154,18 @@ static CgVecs vecs(const bs_problem *P) {
   return CgVecs{P->d_vec, P->d_vec + s, P->d_vec + 2 * s, P->d_vec + 3 * s, P->d_vec + 4 * s};
 }
 
-static int pcg_update_launch(const bs_problem *P, double *x, int init, cudaStream_t s) {
+// The Jacobi-PCG update; bj: then the element-interior blocks of the
+// block-Jacobi preconditioner, which complete z and r.z and advance.
+static int pcg_update_launch(const bs_problem *P, double *x, int init, cudaStream_t s,
+                             bool bj = false) {
   CgVecs v = vecs(P);
   auto kern = k_pcg_update<1>;
   int grid = stream_grid(P->map->NG, 2, kReduceBlock, blocks_per_sm(kern, kReduceBlock));
   if (grid > kMaxPartials / 2) grid = kMaxPartials / 2;
   kern<<<grid, kReduceBlock, 0, s>>>(P->map->NG, v.p, v.Ap, v.dinv, x, v.r, v.z, P->d_partials,
-                                     P->d_counter, P->d_state, init);
+                                     P->d_counter, P->d_state, init, bj ? 1 : 0);
   BS_LAUNCH_CHECK();
+  if (bj) return bj_apply(P, v.r, v.dinv, v.z, init, s);
   return BS_OK;
 }
 
@@ -436,7 +425,8 @@ static int scat_setup(bs_problem *P, const double *x, bool x0, bool precond, dou
 
 // One CG iteration (four launches: the operator with p.Ap, the fused update
 // with r.r, the direction).  ff: the float-float element operator.
-static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, cudaStream_t s) {
+static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, cudaStream_t s,
+                        bool bj = false) {
   const bs_map *m = P->map;
   CgVecs v = vecs(P);
   CgState *st = P->d_state;
@@ -445,7 +435,7 @@ static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, c
                                                  EpAlpha{st, precond ? 1 : 0}, st, s);
   if (rc) return rc;
   if (precond) {
-    rc = pcg_update_launch(P, x, 0, s);
+    rc = pcg_update_launch(P, x, 0, s, bj);
   } else {
     rc = launch_cg_update<double, EpBeta>(m->NG, Scalar<double>{0.0, &st->alpha}, v.p, v.Ap, x,
                                           v.r, P->d_partials, P->d_counter, EpBeta{st}, st, s);
@@ -456,10 +446,10 @@ static int cg_iteration(const bs_problem *P, double *x, bool precond, bool ff, c
 }
 
 static int capture_chunk(bs_problem *P, double *x, bool precond, bool ff, bool scat,
-                         int chunk) {
+                         int chunk, bool bj = false) {
   const void *key[4] = {x, (const void *)(intptr_t)((precond ? 1 : 0) | (ff ? 2 : 0) |
                                                      (g_op_fusion ? 4 : 0) | (scat ? 8 : 0) |
-                                                     (g_op_evenodd ? 16 : 0)),
+                                                     (g_op_evenodd ? 16 : 0) | (bj ? 32 : 0)),
                         (const void *)(intptr_t)chunk,
                         (const void *)P->map};
   if (P->graph && key[0] == P->graph_key[0] && key[1] == P->graph_key[1] &&
@@ -473,7 +463,7 @@ static int capture_chunk(bs_problem *P, double *x, bool precond, bool ff, bool s
   BS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   int rc = BS_OK;
   for (int c = 0; c < chunk && rc == BS_OK; ++c)
-    rc = scat ? scat_iteration(P, precond, ff, cs) : cg_iteration(P, x, precond, ff, cs);
+    rc = scat ? scat_iteration(P, precond, ff, cs) : cg_iteration(P, x, precond, ff, cs, bj);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   if (rc != BS_OK) {
@@ -512,9 +502,13 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
   BS_ARG(NG == 0 || (b && x), "bs_cg_solve: NULL vector");
   cudaStream_t s = as_stream(stream);
   const bool fixed = flags & BS_CG_FIXED_ITERS;
-  const bool precond = flags & BS_CG_JACOBI;
+  const bool bj = flags & BS_CG_BLOCK_JACOBI;
+  const bool precond = (flags & BS_CG_JACOBI) || bj;
   const bool ff = flags & BS_CG_FF_OPERATOR;
   const bool scat = flags & BS_CG_SCATTERED;
+  BS_ARG(!bj || (!scat && !P->d_geo && P->N >= 2 && P->N <= kBjMaxNi + 1),
+         "bs_cg_solve: BS_CG_BLOCK_JACOBI needs affine elements of degree 2..9 in global "
+         "storage");
   double ff_scale = 1.0;  // power of two the FF solve runs scaled by
   CgVecs v = vecs(P);
   CgState *st = P->d_state;
@@ -564,8 +558,9 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
     if (scat) {
       BS_TRY(scat_setup(P, x, flags & BS_CG_X0, precond, tol, maxit, fixed, d_hist, s));
     } else if (precond) {
+      if (bj) BS_TRY(bj_ensure(P, s));
       k_set_state<<<1, 1, 0, s>>>(st, tol * tol, maxit, fixed ? 1 : 0, d_hist);
-      BS_TRY(pcg_update_launch(P, x, 1, s));  // z = dinv r, rr, rz, stop flag
+      BS_TRY(pcg_update_launch(P, x, 1, s, bj));  // z = M^-1 r, rr, rz, stop flag
       BS_TRY(launch_copy<double>(NG, v.z, v.p, s));
     } else {
       BS_TRY(launch_copy<double>(NG, v.r, v.p, s));
@@ -576,13 +571,14 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
     const bool graph = flags & BS_CG_GRAPH;
     const int chunk = maxit < 8 ? (maxit < 1 ? 1 : maxit) : 8;
     int launched = 0;
-    if (graph && maxit > 0) BS_TRY(capture_chunk(P, x, precond, ff, scat, chunk));
+    if (graph && maxit > 0) BS_TRY(capture_chunk(P, x, precond, ff, scat, chunk, bj));
     while (launched < maxit) {
       if (graph) {
         BS_CUDA_TRY(cudaGraphLaunch(P->graph, s));
       } else {
         for (int c = 0; c < chunk; ++c)
-          BS_TRY(scat ? scat_iteration(P, precond, ff, s) : cg_iteration(P, x, precond, ff, s));
+          BS_TRY(scat ? scat_iteration(P, precond, ff, s)
+                      : cg_iteration(P, x, precond, ff, s, bj));
       }
       launched += chunk;
       BS_CUDA_TRY(cudaMemcpyAsync(P->h_state, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));

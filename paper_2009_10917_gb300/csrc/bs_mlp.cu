@@ -639,6 +639,66 @@ int bs_mlp_get_weights(const bs_mlp *m, float *h_W1, float *h_W2) {
   return BS_OK;
 }
 
+// Training-state image: a header, then W1, W2, m1, v1, m2, v2 as stored on
+// the device (n = H * Dp floats each, padded layout).
+struct MlpStateHeader {
+  char magic[8];  // "BSMLPST1"
+  int32_t D, Dp, H, split, step, reserved;
+};
+static const char kStateMagic[8] = {'B', 'S', 'M', 'L', 'P', 'S', 'T', '1'};
+
+int64_t bs_mlp_state_bytes(const bs_mlp *m) {
+  if (!m) return -1;
+  return (int64_t)sizeof(MlpStateHeader) + 6 * (int64_t)m->H * m->Dp * (int64_t)sizeof(float);
+}
+
+int bs_mlp_save_state(const bs_mlp *m, void *h_buf, int64_t nbytes) {
+  if (int rc = check_mlp(m, "bs_mlp_save_state")) return rc;
+  BS_ARG(h_buf != nullptr, "bs_mlp_save_state: NULL buffer");
+  BS_ARG(nbytes >= bs_mlp_state_bytes(m), "bs_mlp_save_state: buffer of %lld bytes, need %lld",
+         (long long)nbytes, (long long)bs_mlp_state_bytes(m));
+  MlpStateHeader h{};
+  memcpy(h.magic, kStateMagic, 8);
+  h.D = m->D;
+  h.Dp = m->Dp;
+  h.H = m->H;
+  h.split = m->split;
+  h.step = m->step;
+  memcpy(h_buf, &h, sizeof(h));
+  // W1, W2, m1, v1, m2, v2 are consecutive in the one allocation
+  const size_t n = (size_t)m->H * m->Dp;
+  BS_CUDA_TRY(cudaDeviceSynchronize());
+  BS_CUDA_TRY(cudaMemcpy(static_cast<char *>(h_buf) + sizeof(h), m->W1, 6 * n * sizeof(float),
+                         cudaMemcpyDeviceToHost));
+  return BS_OK;
+}
+
+int bs_mlp_load_state(bs_mlp *m, const void *h_buf, int64_t nbytes) {
+  if (int rc = check_mlp(m, "bs_mlp_load_state")) return rc;
+  BS_ARG(h_buf != nullptr, "bs_mlp_load_state: NULL buffer");
+  BS_ARG(nbytes >= (int64_t)sizeof(MlpStateHeader), "bs_mlp_load_state: buffer too short");
+  MlpStateHeader h;
+  memcpy(&h, h_buf, sizeof(h));
+  BS_ARG(memcmp(h.magic, kStateMagic, 8) == 0, "bs_mlp_load_state: not a training-state image");
+  BS_ARG(h.D == m->D && h.Dp == m->Dp && h.H == m->H && h.split == m->split,
+         "bs_mlp_load_state: image is D %d H %d split %d, network is D %d H %d split %d", h.D,
+         h.H, h.split, m->D, m->H, m->split);
+  BS_ARG(h.step >= 0, "bs_mlp_load_state: negative step count");
+  BS_ARG(nbytes >= bs_mlp_state_bytes(m), "bs_mlp_load_state: buffer of %lld bytes, need %lld",
+         (long long)nbytes, (long long)bs_mlp_state_bytes(m));
+  const size_t n = (size_t)m->H * m->Dp;
+  BS_CUDA_TRY(cudaDeviceSynchronize());
+  BS_CUDA_TRY(cudaMemcpy(m->W1, static_cast<const char *>(h_buf) + sizeof(h),
+                         6 * n * sizeof(float), cudaMemcpyHostToDevice));
+  m->step = h.step;
+  m->odd_step = -1;  // derived operands are stale
+  m->int_step = -1;
+  k_refresh<<<stream_grid((int64_t)n, 1, 256, 8), 256>>>(m->H, m->Dp, m->split, m->W1, m->W2,
+                                                          m->W1b, m->W2b, m->W2tb);
+  BS_CUDA_TRY(cudaDeviceSynchronize());
+  return BS_OK;
+}
+
 int bs_mlp_forward(bs_mlp *m, int64_t B, const float *d_X, float *d_Y, int32_t flags,
                    void *stream) {
   if (int rc = check_mlp(m, "bs_mlp_forward")) return rc;

@@ -136,6 +136,7 @@ static void free_problem(bs_problem *p) {
   cudaFree(p->d_f32);
   cudaFree(p->d_Lvec);
   cudaFree(p->d_owner);
+  cudaFree(p->d_bj);
   if (p->h_state) cudaFreeHost(p->h_state);
   free(p);
 }

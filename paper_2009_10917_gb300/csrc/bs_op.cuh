@@ -448,4 +448,5 @@ struct bs_problem {
   float *d_f32;                   // 4 x [NG + 8] FP32 vectors (refined solver), lazily
   double *d_Lvec;                 // 6 x [NL + 2 rounded up to even] scattered CG vectors, lazily
   uint8_t *d_owner;               // [NL + 16] 1 at the lowest local copy of each node, lazily
+  void *d_bj;                     // block-Jacobi tables and per-element flags, lazily
 };

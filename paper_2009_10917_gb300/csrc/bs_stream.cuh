@@ -100,10 +100,34 @@ struct CgState {
   int fallback;   // learned FPCG: 1 if this iteration's correction was rejected
   int nfallback;  // learned FPCG: corrections rejected so far
   double *hist;   // optional [3*(maxit+1)] alpha, beta, rr per iteration
+  double rr_next; // block-Jacobi PCG: r.r and the Jacobi part of r.z of the
+  double rz_next; // update, held until the interior blocks are solved
 };
 
 __device__ __forceinline__ bool cg_halted(const CgState *st) {
   return st != nullptr && *((volatile const int *)&st->done) != 0;
+}
+
+// The end of a CG iteration (Algorithm 1, steps 10-11 bookkeeping): record
+// alpha, beta and r.r in the optional history, take beta and the new r.r,
+// count the iteration and set the stop flag.
+__device__ __forceinline__ void cg_advance(CgState *st, double rr_new, double beta) {
+  const int j = st->iter;
+  if (st->hist) {
+    st->hist[3 * j] = st->alpha;
+    st->hist[3 * j + 1] = beta;
+    st->hist[3 * j + 2] = rr_new;
+  }
+  st->beta = beta;
+  st->beta_f = (float)beta;
+  st->rr = rr_new;
+  st->iter = j + 1;
+  if (!isfinite(rr_new) || !isfinite(beta))
+    st->done = 2;
+  else if (!st->fixed && rr_new <= st->eps)
+    st->done = 1;
+  else if (j + 1 >= st->maxit)
+    st->done = 3;
 }
 
 }  // namespace bs

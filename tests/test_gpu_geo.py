@@ -68,6 +68,25 @@ def test_geo_float_float_apply_matches_oracle(K, N):
         assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("shrink", [2.0 ** -20, 2.0 ** -28])
+def test_geo_float_float_on_a_small_domain(shrink):
+    """The geometric factors themselves scale with the mesh: G ~ w h / 2 and
+    lambda w det J ~ lambda h^3.  On a domain shrunk by 2^-20 and by 2^-28
+    (stiffness factors near 2^-30, all inside the float-pair window that
+    starts at 2^-102) the float-float kernel still agrees with the oracle
+    within 1e-11 max|A p|.  (The mass term then lies below the stiffness
+    term's rounding on both sides, so A p is the stiffness part.)"""
+    m = synth.Mesh(2, 4, seed=3, perturb=0.2)
+    c = synth.lognormal(m.E, 4)
+    V = m.verts() * shrink
+    Z = bs.Map(m.E, 4, m.NG, m.ids)
+    P = bs.Problem(Z, m.h, 0.5, c, verts=V)
+    p = synth.uniform(m.NG, 5)
+    got = P.apply_A_ff(cuda(p)).cpu().numpy()
+    want = oracle.apply_A_geo(m.E, 4, 0.5, V, m.ids, m.NG, p, c)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
 def test_geo_on_cubes_matches_the_affine_problem():
     m, Z, P, c, V = make(3, 5, delta=0.0)
     Pa = bs.Problem(Z, m.h, 0.5, c)

@@ -228,6 +228,31 @@ def test_judge_switches_a_bad_network_to_jacobi():
     assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(b.cpu().numpy())
 
 
+def test_judge_switches_near_where_the_oracle_judge_does():
+    """The oracle's flexible PCG carries the same judge (checked every 8
+    iterations, patience max(1024, 16 N_G^(1/3))).  On the stalling network
+    both switch to Jacobi and converge.  The bf16 network's products round in
+    different FP32 orders on the two sides, and a stalled flexible CG
+    amplifies such differences, so the r.r histories -- and with them the
+    last progress mark -- need not coincide: the switch iterations must
+    agree within a tenth (at least 64 iterations), the totals within a
+    quarter."""
+    coef = synth.lognormal(4 ** 3, 2)
+    m, Z, P = _problem(4, 3, 1e-2, coef)
+    W1, W2 = weights(64, 64, 9)
+    net = bs.MLP(W1, 3 * W2)
+    b = synth.uniform(m.NG, 3)
+    x, info = bs.fpcg_learned(P, net, torch.from_numpy(b).cuda(), tol=1e-8, maxit=20000,
+                              flags=bs.BS_CG_GRAPH)
+    xo, ito, hr, fb, sw = oracle.fpcg_judged(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, W1, 3 * W2,
+                                             prec=oracle.PREC_BF16, tol=1e-8, maxit=20000,
+                                             coef=coef)
+    assert info["rc"] == 0 and info["outer"] > 0 and sw > 0
+    assert info["outer"] % 8 == 0
+    assert abs(info["outer"] - sw) <= max(64, 0.1 * sw), (info["outer"], sw)
+    assert abs(info["iterations"] - ito) <= 0.25 * ito, (info["iterations"], ito)
+
+
 def test_trained_network_gain():
     """What the trained network gains over the method without it: on a
     degree-5 mesh with lognormal coefficients (lambda = 1e-2), flexible PCG
@@ -301,3 +326,41 @@ def test_tcgen05_engine_matches_mma_sync(split):
             assert torch.equal(a, c)
         else:
             assert a == c
+
+
+def test_checkpoint_resumes_training_bitwise(tmp_path):
+    """Training state saved after 12 Adam steps and loaded into a network
+    created with other weights: 12 more steps on both give bitwise the same
+    masters as 24 uninterrupted steps (weights, both Adam moments and the
+    step count's bias correction all travel in the image)."""
+    D, H, B = 216, 256, 128
+    W1, W2 = weights(D, H, 31)
+    X = torch.from_numpy(synth.uniform(24 * B * D, 32).reshape(24 * B, D).astype(np.float32)).cuda()
+    T = torch.from_numpy(synth.uniform(24 * B * D, 33).reshape(24 * B, D).astype(np.float32)).cuda()
+    for split in (False, True):
+        a = bs.MLP(W1, W2, split=split)
+        for k in range(12):
+            a.train_step(X[k * B:(k + 1) * B], T[k * B:(k + 1) * B], 1e-3)
+        path = tmp_path / f"state_{int(split)}.bin"
+        a.save(path)
+        V1, V2 = weights(D, H, 34)
+        c = bs.MLP(V1, V2, split=split)
+        c.load(path)
+        assert all(np.array_equal(u, v) for u, v in zip(c.weights(), a.weights()))
+        for k in range(12, 24):
+            a.train_step(X[k * B:(k + 1) * B], T[k * B:(k + 1) * B], 1e-3)
+            c.train_step(X[k * B:(k + 1) * B], T[k * B:(k + 1) * B], 1e-3)
+        for u, v in zip(a.weights(), c.weights()):
+            assert np.array_equal(u.view(np.uint32), v.view(np.uint32))
+        ya = a.forward(X[:B]).cpu().numpy()
+        yc = c.forward(X[:B]).cpu().numpy()
+        assert np.array_equal(ya.view(np.uint32), yc.view(np.uint32))
+    # an image of another shape or mode is refused
+    img = bs.MLP(W1, W2).save_state()
+    with pytest.raises(bs.BSError):
+        bs.MLP(W1, W2, split=True).load_state(img)
+    Wa, Wb = weights(D, 128, 35)
+    with pytest.raises(bs.BSError):
+        bs.MLP(Wa, Wb).load_state(img)
+    with pytest.raises(bs.BSError):
+        bs.MLP(W1, W2).load_state(img[:100])

@@ -877,3 +877,125 @@ def test_omp_loops_match_the_single_threaded_oracle():
     g = np.full(m.NG, np.nan)
     om.gather(rs, ci, ql, g)
     assert np.array_equal(g.view(np.uint64), oracle.gather(ids, ql, m.NG).view(np.uint64))
+
+
+def _judge_case():
+    """A random, nonlinear full-size correction that stalls flexible CG on a
+    degree-3 4^3 mesh with lognormal coefficients (lambda = 1e-2)."""
+    m = synth.Mesh(4, 3, seed=1)
+    coef = synth.lognormal(m.E, 2)
+    W1 = (synth.uniform(64 * 64, 9, 0).reshape(64, 64) * np.sqrt(3.0 / 64)).astype(np.float32)
+    W2 = (synth.uniform(64 * 64, 9, 1).reshape(64, 64) * np.sqrt(3.0 / 64) * 3).astype(np.float32)
+    return m, coef, W1, W2, synth.uniform(m.NG, 3)
+
+
+def test_fpcg_judge_switches_by_its_rule_and_restarts_as_jacobi_pcg():
+    """The Jacobi judge (reading of the learned solver's safeguard): checked
+    every 8 iterations, it records progress when r.r has fallen to a quarter
+    of the last progress mark and, after max(1024, 16 N_G^(1/3)) iterations
+    without progress, restarts from the current x with z = D^-1 r, p = z.
+    Pinned three ways: the switch iteration follows from the r.r history by
+    that rule; the iterations after the switch are those of a dense numpy
+    Jacobi-PCG started from the switch iterate (independent assembly); and the
+    solve then converges to the true residual tolerance."""
+    m, coef, W1, W2, b = _judge_case()
+    lam, tol = 1e-2, 1e-8
+    x, it, hr, fb, sw = oracle.fpcg_judged(m.E, 3, m.h, lam, m.ids, m.NG, b, W1, W2, tol=tol,
+                                           maxit=20000, coef=coef)
+    stall = oracle.judge_stall(m.NG)
+    assert stall == 1024 and sw > 0 and sw % 8 == 0
+    mark_rr, mark_it, first = np.inf, 0, 0
+    for j in range(8, it + 1, 8):
+        if hr[j] <= 0.25 * mark_rr:
+            mark_rr, mark_it = hr[j], j
+        elif j - mark_it >= stall:
+            first = j
+            break
+    assert first == sw
+    # the switch iterate: the same solve stopped at the switch
+    xs, its, hrs, _, sws = oracle.fpcg_judged(m.E, 3, m.h, lam, m.ids, m.NG, b, W1, W2, tol=tol,
+                                              maxit=sw, coef=coef)
+    assert its == sw and sws == sw and np.array_equal(hrs, hr[:sw + 1])
+    A = fem_ref.assemble(m, lam, coef)
+    d = np.diag(A)
+    r = b - A @ xs
+    z = r / d
+    p = z.copy()
+    rz = r @ z
+    dense = []
+    for _ in range(12):
+        Ap = A @ p
+        a = rz / (p @ Ap)
+        r = r - a * Ap
+        dense.append(r @ r)
+        z = r / d
+        rzn = r @ z
+        p = z + (rzn / rz) * p
+        rz = rzn
+    np.testing.assert_allclose(hr[sw + 1:sw + 13], dense, rtol=1e-6)
+    rt = b - oracle.apply_A(m.E, 3, m.h, lam, m.ids, m.NG, x, coef=coef)
+    assert it < 20000 and np.linalg.norm(rt) <= 1.5 * tol * np.linalg.norm(b)
+
+
+def test_fpcg_judge_leaves_a_working_correction_alone():
+    """With a zero correction (Jacobi-PCG converging steadily) the judge never
+    fires: the judged solve is the unjudged one, iterate for iterate."""
+    m, coef, W1, _, b = _judge_case()
+    W2 = np.zeros((64, 64), np.float32)
+    x, it, hr, fb, sw = oracle.fpcg_judged(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, W1, W2, tol=1e-10,
+                                           maxit=20000, coef=coef)
+    x2, it2, hr2, fb2 = oracle.fpcg(m.E, 3, m.h, 1e-2, m.ids, m.NG, b, W1, W2, tol=1e-10,
+                                    maxit=20000, coef=coef)
+    assert sw == 0 and it == it2 and np.array_equal(hr, hr2) and np.array_equal(x, x2)
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_pcg_block_jacobi_matches_dense_block_jacobi_pcg(N):
+    """The oracle's block-Jacobi PCG (element interiors solved by Cholesky of
+    the element matrix's interior block, Jacobi elsewhere) against a dense
+    numpy PCG whose preconditioner inverts the interior blocks of the
+    independently assembled global matrix, with lognormal coefficients: the
+    same r.r history, the same iteration count, and a solution of the
+    system."""
+    m = synth.Mesh(2, N, seed=1)
+    coef = synth.lognormal(m.E, 6)
+    lam = 1e-2
+    ids = m.ids
+    A = fem_ref.assemble(m, lam, coef)
+    keep = np.arange(m.NG)
+    b = synth.uniform(m.NG, 8)
+    x, it, rr = oracle.pcg_block_jacobi(m.E, N, m.h, lam, ids, m.NG, b, tol=1e-10, maxit=2000,
+                                        coef=coef)
+    Ak = A[np.ix_(keep, keep)]
+    bk = b[keep]
+    pos = {g: i for i, g in enumerate(keep)}
+    val = np.bincount(ids[ids >= 0], minlength=m.NG)
+    Minv = np.diag(1.0 / np.diag(Ak))
+    I = _interior_index(N)
+    for e in range(m.E):
+        g = [pos[v] for v in ids[e * m.Np:(e + 1) * m.Np][I] if v >= 0 and val[v] == 1]
+        if g:
+            Minv[np.ix_(g, g)] = np.linalg.inv(Ak[np.ix_(g, g)])
+    xd = np.zeros(keep.size)
+    r = bk.copy()
+    z = Minv @ r
+    p = z.copy()
+    rz = r @ z
+    hist = [r @ r]
+    while hist[-1] > 1e-20 * (bk @ bk) and len(hist) < 2000:
+        Ap = Ak @ p
+        a = rz / (p @ Ap)
+        xd += a * p
+        r -= a * Ap
+        hist.append(r @ r)
+        z = Minv @ r
+        rzn = r @ z
+        p = z + rzn / rz * p
+        rz = rzn
+    k = min(len(hist), 10)
+    np.testing.assert_allclose(rr[:k], hist[:k], rtol=1e-8)
+    assert abs(it - (len(hist) - 1)) <= 1
+    np.testing.assert_allclose(x[keep], np.linalg.solve(Ak, bk), rtol=0, atol=1e-8 * np.abs(xd).max())
+    _, itj, _ = oracle.pcg_jacobi(m.E, N, m.h, lam, ids, m.NG, b, tol=1e-10, maxit=2000,
+                                  coef=coef)
+    assert it <= itj
