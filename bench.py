@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-tolerance runs")
     ap.add_argument("--workload", default="stream",
-                    choices=["stream", "cg", "batched", "learned", "sweep"],
+                    choices=["stream", "cg", "batched", "learned", "sweep", "op"],
                     help="stream: the BS step (default); cg: only the CG solves on --cg-mesh; "
                          "batched: 256 uneven solves, batched vs one at a time; "
                          "learned: learned-preconditioner FPCG vs Jacobi-PCG and plain CG; "
@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--sweep-runs", type=int, default=20,
                     help="sweep: back-to-back runs per size")
     ap.add_argument("--sweep-out", default=None, help="sweep: also write the JSON here")
+    ap.add_argument("--op", default="gather", choices=OPS,
+                    help="op: the one operation to run --reps times (for a profiler)")
+    ap.add_argument("--reps", type=int, default=3, help="op: calls of the operation")
     ap.add_argument("--learned-mesh", default="5,64", help="N,K of the learned workload")
     ap.add_argument("--no-plain", action="store_true",
                     help="learned workload: skip the (long) unpreconditioned CG solve")
@@ -852,6 +855,39 @@ def sweep_section(args):
             "gather_scatter_N7_K_sweep": ksweep, "gather_scatter_N7_fit": fits}
 
 
+def run_one_op(args):
+    """One BS operation, --reps calls on the --log2n vectors or the --mesh
+    mesh, nothing else: a short, fixed launch sequence for a profiler."""
+    import torch
+
+    from paper_2009_10917_gb300 import bs, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    op, n = args.op, 1 << args.log2n
+    if op in ("scatter", "gather"):
+        N, K = (int(v) for v in args.mesh.split(","))
+        m = synth.Mesh(K, N, seed=1)
+        Z = bs.Map(m.E, N, m.NG, m.ids)
+        qG = torch.from_numpy(synth.uniform(m.NG, 2)).cuda()
+        qL = torch.from_numpy(synth.uniform(m.NL, 3)).cuda()
+        for _ in range(args.reps):
+            Z.scatter(qG, qL) if op == "scatter" else Z.gather(qL, qG)
+    else:
+        x, y, z, w = (torch.from_numpy(synth.uniform(n, 1, s)).cuda() for s in range(4))
+        for _ in range(args.reps):
+            if op == "copy":
+                bs.copy(x, y)
+            elif op == "axpy":
+                bs.axpy(0.5, x, 1.0, y)
+            elif op == "norm":
+                bs.norm(x)
+            elif op == "dot":
+                bs.dot(x, y)
+            else:
+                bs.cg_update(1e-3, x, y, z, w)
+    torch.cuda.synchronize()
+    print(json.dumps({"op": op, "reps": args.reps, "done": True}), flush=True)
+
+
 def run_cg_only(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -992,6 +1028,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "cg":
         run_cg_only(a)
+    elif a.workload == "op":
+        run_one_op(a)
     elif a.workload == "sweep":
         res = sweep_section(a)
         line = {"metric": "per-op HBM GB/s over sizes; T0/Wmax fit (Sec. 4, Table 2)",

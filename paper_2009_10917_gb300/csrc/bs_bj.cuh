@@ -13,25 +13,37 @@
 //   A_II^-1 = (V x V x V) diag(1 / (c_e (h/2)(mu_a + mu_b + mu_c) + lambda (h/2)^3))
 //             (V x V x V)^T,
 // i.e. three 1-D transforms, a diagonal scaling and three transforms back,
-// 6 (N-1) multiply-adds per interior node.  The transforms run in FP32 on
-// values normalised per element by a power of two (a preconditioner needs no
-// more precision, and the FP32 pipes are 64 times GB300's FP64 rate); the
-// result is scaled back exactly.
+// 6 (N-1) multiply-adds per interior node.  They run in float-float
+// arithmetic on the FP32 pipes (64 times GB300's FP64 rate): inputs split
+// exactly into float pairs by integer operations, error-free products and
+// TwoSum accumulation, about 2^-46 relative.  Plain FP32 would not do: CG with
+// a preconditioner perturbed at 1e-7 lost up to a third more iterations at
+// tolerance 1e-10 on low degrees.  Residuals whose RMS lies outside
+// [2^-120, 2^120] are scaled by a power of two first (exact both ways).
 #pragma once
 
 #include <cmath>
 #include <vector>
 
-#include "bs_op.cuh"
+#include "bs_op_ff.cuh"
 
 namespace bs {
 
 constexpr int kBjMaxNi = 8;  // interior points per direction: N <= 9
 
+// V[m * ni + a] = component m of eigenvector a and M[a + ni (b + ni c)] =
+// mu_a + mu_b + mu_c, as float pairs (h + l) of the double values.
 struct BjTab {
-  float V[kBjMaxNi * kBjMaxNi];  // V[m * ni + a]: component m of eigenvector a
-  float mu[kBjMaxNi];
+  float Vh[kBjMaxNi * kBjMaxNi], Vl[kBjMaxNi * kBjMaxNi];
+  float Mh[kBjMaxNi * kBjMaxNi * kBjMaxNi], Ml[kBjMaxNi * kBjMaxNi * kBjMaxNi];
 };
+constexpr size_t kBjQualOffset = (sizeof(BjTab) + 255) / 256 * 256;
+
+// (h, l) renormalised so that |l| <= ulp(h) / 2 (Fast2Sum).
+__device__ __forceinline__ FF ff_norm(FF a) {
+  const float h = a.hi + a.lo;
+  return FF{h, a.lo - (h - a.hi)};
+}
 
 // Eigen-decomposition of a symmetric n x n matrix A (row-major, destroyed) by
 // cyclic Jacobi rotations: A = Q diag(lam) Q^T, Q[m * n + a] = component m of
@@ -99,28 +111,43 @@ __global__ void k_bj_qualify(int64_t E, int N, const int32_t *__restrict__ ids,
 // thread per interior node (two when ni^3 > 256).
 template <int NI>
 __global__ void __launch_bounds__(256)
-    k_bj_apply(int64_t E, int N, const int32_t *__restrict__ ids, const uint8_t *__restrict__ qual,
-               const double *__restrict__ coef, float g, float mlam, const BjTab *__restrict__ tab,
-               const double *__restrict__ r, const double *__restrict__ dinv,
-               double *__restrict__ z, double *partials, unsigned int *counter, CgState *st,
-               int init) {
+    k_bj_apply(int64_t E, int64_t NG, int N, const int32_t *__restrict__ ids,
+               const uint8_t *__restrict__ qual, const double *__restrict__ coef, double g,
+               double mlam, const BjTab *__restrict__ tab, const double *__restrict__ r,
+               const double *__restrict__ dinv, double *__restrict__ z, double *partials,
+               unsigned int *counter, CgState *st, int init) {
   constexpr int NN = NI * NI * NI;
   constexpr int EPB = NN >= 256 ? 1 : 256 / NN;
   constexpr int PER = (NN + 255) / 256;
-  __shared__ float s_a[EPB * NN], s_b[EPB * NN];
-  __shared__ float s_V[NI * NI], s_mu[NI];
-  __shared__ int s_ex[EPB];
+  __shared__ float s_ah[EPB * NN], s_al[EPB * NN], s_bh[EPB * NN], s_bl[EPB * NN];
+  __shared__ float s_Vh[NI * NI], s_Vl[NI * NI];
+  __shared__ float s_ch[EPB], s_cl[EPB];
   if (!init && cg_halted(st)) return;
-  for (int t = threadIdx.x; t < NI * NI; t += 256) s_V[t] = tab->V[t];
-  if (threadIdx.x < NI) s_mu[threadIdx.x] = tab->mu[threadIdx.x];
+  for (int t = threadIdx.x; t < NI * NI; t += 256) {
+    s_Vh[t] = tab->Vh[t];
+    s_Vl[t] = tab->Vl[t];
+  }
+  // a power of two bringing the residual's RMS near 1, when it lies far from it
+  const double rr = init ? st->rr : st->rr_next;
+  int k = 0;
+  if (rr > 0.0 && isfinite(rr) && NG > 0) {
+    const int e = ilogb(rr / (double)NG) / 2;
+    if (e > 120 || e < -120) k = e;
+  }
+  const double down = ldexp(1.0, -k), up = ldexp(1.0, k);
+  const FF ml = ff_split(mlam);
   const int Nq = N + 1, Np = Nq * Nq * Nq;
   double acc = 0.0;
   for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < E; e0 += (int64_t)gridDim.x * EPB) {
+    if (threadIdx.x < EPB) {
+      const int64_t e = e0 + threadIdx.x;
+      const FF c = ff_split((coef && e < E ? coef[e] : 1.0) * g);
+      s_ch[threadIdx.x] = c.hi;
+      s_cl[threadIdx.x] = c.lo;
+    }
     int32_t gid[PER];
     double rv[PER];
     bool on[PER];
-    if (threadIdx.x < EPB) s_ex[threadIdx.x] = -2000;
-    __syncthreads();
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int f = threadIdx.x + 256 * u, slot = f / NN, q = f - slot * NN;
@@ -128,25 +155,25 @@ __global__ void __launch_bounds__(256)
       on[u] = f < EPB * NN && e < E && qual[e];
       gid[u] = -1;
       rv[u] = 0.0;
+      FF x{0.f, 0.f};
       if (on[u]) {
         const int a = q % NI, b = (q / NI) % NI, c = q / (NI * NI);
         gid[u] = ids[e * Np + (a + 1) + Nq * ((b + 1) + Nq * (c + 1))];
         rv[u] = r[gid[u]];
-        if (rv[u] != 0.0) atomicMax(&s_ex[slot], ilogb(rv[u]));
+        x = ff_split(k ? rv[u] * down : rv[u]);
+      }
+      if (f < EPB * NN) {
+        s_ah[f] = x.hi;
+        s_al[f] = x.lo;
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int f = threadIdx.x + 256 * u;
-      if (f < EPB * NN) s_a[f] = on[u] ? (float)ldexp(rv[u], -s_ex[f / NN]) : 0.f;
-    }
-    __syncthreads();
-    // (V x V x V)^T: along a, then b, then c (s_a -> s_b -> s_a -> s_b)
+    // (V x V x V)^T along a, b, c; the scaling; V x V x V along a, b, c.
+    // Buffers alternate a -> b -> a ...; after six passes the result is in a.
 #pragma unroll
     for (int pass = 0; pass < 6; ++pass) {
-      const float *in = (pass & 1) ? s_b : s_a;
-      float *out = (pass & 1) ? s_a : s_b;
+      const float *inh = (pass & 1) ? s_bh : s_ah, *inl = (pass & 1) ? s_bl : s_al;
+      float *outh = (pass & 1) ? s_ah : s_bh, *outl = (pass & 1) ? s_al : s_bl;
       const int dim = pass % 3;
       const bool fwd = pass < 3;
 #pragma unroll
@@ -154,31 +181,41 @@ __global__ void __launch_bounds__(256)
         const int f = threadIdx.x + 256 * u;
         if (f < EPB * NN) {
           const int slot = f / NN, q = f - slot * NN;
-          const int a = q % NI, b = (q / NI) % NI, c = q / (NI * NI);
-          const int ix = dim == 0 ? a : (dim == 1 ? b : c);
+          const int ix = dim == 0 ? q % NI : (dim == 1 ? (q / NI) % NI : q / (NI * NI));
           const int stride = dim == 0 ? 1 : (dim == 1 ? NI : NI * NI);
-          const float *line = in + slot * NN + (q - ix * stride);
-          float s = 0.f;
+          const int base = slot * NN + (q - ix * stride);
+          FF s{0.f, 0.f};
 #pragma unroll
-          for (int m = 0; m < NI; ++m)
-            s = fmaf(fwd ? s_V[m * NI + ix] : s_V[ix * NI + m], line[m * stride], s);
-          if (pass == 2) {  // the diagonal scaling, between the two halves
-            const float ce = coef ? (float)coef[e0 + slot < E ? e0 + slot : 0] : 1.0f;
-            s = s / fmaf(ce * g, s_mu[a] + s_mu[b] + s_mu[c], mlam);
+          for (int m = 0; m < NI; ++m) {
+            const int v = fwd ? m * NI + ix : ix * NI + m;
+            ff_fma(s, s_Vh[v], s_Vl[v], inh[base + m * stride], inl[base + m * stride]);
           }
-          out[f] = s;
+          s = ff_norm(s);
+          if (pass == 2) {  // divide by d = c_e (h/2)(mu_a + mu_b + mu_c) + lambda (h/2)^3
+            FF d = ml;
+            ff_fma(d, s_ch[slot], s_cl[slot], __ldg(tab->Mh + q), __ldg(tab->Ml + q));
+            d = ff_norm(d);
+            const float x0 = 1.0f / d.hi;  // 1/d = x0 (1 + err), err from d x0 exactly
+            const float p = d.hi * x0;
+            const float err = ((1.0f - p) - fmaf(d.hi, x0, -p)) - d.lo * x0;
+            FF o{0.f, 0.f};
+            ff_fma(o, s.hi, s.lo, x0, x0 * err);
+            s = ff_norm(o);
+          }
+          outh[f] = s.hi;
+          outl[f] = s.lo;
         }
       }
       __syncthreads();
     }
-    // after six passes the result is in s_a
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       if (!on[u]) continue;
       const int f = threadIdx.x + 256 * u;
-      const double zv = ldexp((double)s_a[f], s_ex[f / NN]);
+      double zv = ff_widen(s_ah[f]) + ff_widen(s_al[f]);
+      if (k) zv = zv * up;
       z[gid[u]] = zv;
-      acc = fma(rv[u], zv - dinv[gid[u]] * rv[u], acc);
+      acc = fma(rv[u], fma(-dinv[gid[u]], rv[u], zv), acc);
     }
     __syncthreads();
   }
@@ -196,7 +233,8 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Device tables (V, mu) and per-element flags of a problem, built on first use.
+// Device tables (V and the eigenvalue sums, as float pairs) and per-element
+// flags of a problem, built on first use.
 inline int bj_ensure(bs_problem *P, cudaStream_t s) {
   if (P->d_bj) return BS_OK;
   const int N = P->N, Nq = N + 1, ni = N - 1;
@@ -210,17 +248,26 @@ inline int bj_ensure(bs_problem *P, cudaStream_t s) {
                               std::sqrt(tab.w[a + 1] * tab.w[b + 1]);
   sym_eig(ni, B.data(), Q.data(), mu.data());
   BjTab h{};
-  for (int m = 0; m < ni; ++m) {
+  auto split = [](double v, float *hi, float *lo) {
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
+  };
+  for (int m = 0; m < ni; ++m)
     for (int a = 0; a < ni; ++a)
-      h.V[m * ni + a] = (float)(Q[(size_t)m * ni + a] / std::sqrt(tab.w[m + 1]));
-    h.mu[m] = (float)mu[m];
-  }
+      split(Q[(size_t)m * ni + a] / std::sqrt(tab.w[m + 1]), &h.Vh[m * ni + a],
+            &h.Vl[m * ni + a]);
+  for (int c = 0; c < ni; ++c)
+    for (int b = 0; b < ni; ++b)
+      for (int a = 0; a < ni; ++a) {
+        const int q = a + ni * (b + ni * c);
+        split(mu[a] + mu[b] + mu[c], &h.Mh[q], &h.Ml[q]);
+      }
   const int64_t E = P->map->E;
   void *mem = nullptr;
-  BS_CUDA_TRY(cudaMalloc(&mem, 512 + (size_t)(E > 0 ? E : 1)));
+  BS_CUDA_TRY(cudaMalloc(&mem, kBjQualOffset + (size_t)(E > 0 ? E : 1)));
   P->d_bj = mem;
   BS_CUDA_TRY(cudaMemcpy(mem, &h, sizeof(h), cudaMemcpyHostToDevice));
-  uint8_t *qual = static_cast<uint8_t *>(mem) + 512;
+  uint8_t *qual = static_cast<uint8_t *>(mem) + kBjQualOffset;
   if (E > 0) {
     k_bj_qualify<<<stream_grid(E, 1, 256, 4), 256, 0, s>>>(E, N, P->map->d_ids,
                                                            P->map->d_row_starts, qual);
@@ -235,14 +282,14 @@ inline int bj_apply(const bs_problem *P, const double *r, const double *dinv, do
   const int64_t E = P->map->E;
   if (E == 0) return BS_OK;
   const BjTab *tab = static_cast<const BjTab *>(P->d_bj);
-  const uint8_t *qual = static_cast<const uint8_t *>(P->d_bj) + 512;
-  const float g = (float)(0.5 * P->h), mlam = (float)(P->lambda * 0.125 * P->h * P->h * P->h);
+  const uint8_t *qual = static_cast<const uint8_t *>(P->d_bj) + kBjQualOffset;
+  const double g = 0.5 * P->h, mlam = P->lambda * (0.5 * P->h) * (0.5 * P->h) * (0.5 * P->h);
   auto launch = [&](auto kern, int nn) -> int {
     const int epb = nn >= 256 ? 1 : 256 / nn;
     int grid = stream_grid((E + epb - 1) / epb, 1, 1, blocks_per_sm(kern, 256));
     if (grid > kMaxPartials) grid = kMaxPartials;
-    kern<<<grid, 256, 0, s>>>(E, P->N, P->map->d_ids, qual, P->d_coef, g, mlam, tab, r, dinv, z,
-                              P->d_partials, P->d_counter, P->d_state, init);
+    kern<<<grid, 256, 0, s>>>(E, P->map->NG, P->N, P->map->d_ids, qual, P->d_coef, g, mlam, tab,
+                              r, dinv, z, P->d_partials, P->d_counter, P->d_state, init);
     BS_LAUNCH_CHECK();
     return BS_OK;
   };

@@ -15,9 +15,16 @@
 // Measured alternatives that were slower on GB300 (N=7, 48^3, permuted
 // elements): one thread per row (51% of HBM peak), cp.async double buffering
 // (54%), tiles per warp (61%), row starts staged in shared memory (57%),
-// register prefetch of the next tile (66%); this form reaches about 70%.  The
-// q_L reads are 64-byte element-row segments scattered by the element
-// permutation, which bounds the gather below a pure stream.
+// register prefetch of the next tile (66%); this form reaches about 70%.
+// Later measurements: tiles of 1024 to 16384 entries, row starts or the next
+// tile's indices held in registers, two tiles interleaved per block, and
+// contiguous tile ranges per block were none more than 3% faster (several
+// much slower); an unpermuted element order runs no faster (locality is not
+// the limit: ncu shows full occupancy, DRAM bytes at the algorithmic count
+// and warps waiting on the dependent colIds -> q_L loads).  Loading q_L
+// through the read-only data path (__ldg) instead of as streaming loads gave
+// 6%, probably because an element row read by two neighbouring tiles of the
+// same wave then stays in L1.
 #pragma once
 
 #include "bs_gs.cuh"
@@ -75,7 +82,7 @@ __device__ __forceinline__ void gather_tile(int2 lo, int2 hi,
       }
       T v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = c[u] >= 0 ? __ldcs(qL + c[u]) : T(0);
+      for (int u = 0; u < U; ++u) v[u] = c[u] >= 0 ? __ldg(qL + c[u]) : T(0);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int kk = threadIdx.x + u * kGatherBlock;

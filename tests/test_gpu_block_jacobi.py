@@ -3,10 +3,12 @@ against the oracle's block-Jacobi PCG, which factors every interior block
 A_II of c_e S_e + lambda M_e by Cholesky (the oracle is pinned against a dense
 numpy PCG with the same preconditioner).
 
-The library applies A_II^-1 by fast diagonalisation in FP32 (about 1e-7
-relative per application), so its r.r history follows the oracle's to about
-1e-5 relative over the first iterations and the iteration counts to tolerance
-agree within max(3, 2%); the solution satisfies the FP64 true residual bound.
+The library applies A_II^-1 by fast diagonalisation in float-float arithmetic
+(about 2^-46 relative per application) where the oracle uses Cholesky in
+FP64; the two differ by rounding, so the r.r histories agree to 1e-5 relative
+over the first iterations and the iteration counts to tolerance within
+max(3, 2%) (the CG iteration-count bound); the solution satisfies the FP64
+true residual bound.
 """
 import numpy as np
 import pytest
@@ -56,7 +58,10 @@ def test_block_jacobi_follows_the_oracle(K, N, masked):
     r = b - oracle.apply_A(m.E, N, m.h, lam, ids, NG, x.cpu().numpy(), coef)
     assert np.linalg.norm(r) <= 2e-10 * np.linalg.norm(b)
     _, itj, _ = oracle.pcg_jacobi(m.E, N, m.h, lam, ids, NG, b, tol=1e-10, maxit=5000, coef=coef)
-    assert info["iterations"] < itj
+    if N == 2:  # a one-node interior: the block is the diagonal, block Jacobi is Jacobi
+        assert abs(info["iterations"] - itj) <= max(3, 0.02 * itj)
+    else:
+        assert info["iterations"] < itj
 
 
 @pytest.mark.parametrize("flags", [bs.BS_CG_GRAPH, bs.BS_CG_GRAPH | bs.BS_CG_FF_OPERATOR])
