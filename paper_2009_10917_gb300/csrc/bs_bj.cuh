@@ -138,7 +138,25 @@ __global__ void __launch_bounds__(256)
   const FF ml = ff_split(mlam);
   const int Nq = N + 1, Np = Nq * Nq * Nq;
   double acc = 0.0;
-  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < E; e0 += (int64_t)gridDim.x * EPB) {
+  // the map entries (and qualification flags) of a group of elements: loaded
+  // one group ahead, so that the dependent loads of r and D^-1 are the only
+  // memory latency a group waits for
+  int32_t nid[PER];
+  uint8_t nq[PER];
+  auto load_ids = [&](int64_t e0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int f = threadIdx.x + 256 * u, slot = f / NN, q = f - slot * NN;
+      const int64_t e = e0 + slot;
+      const bool valid = f < EPB * NN && e < E;
+      const int a = q % NI, b = (q / NI) % NI, c = q / (NI * NI);
+      nid[u] = valid ? ids[e * Np + (a + 1) + Nq * ((b + 1) + Nq * (c + 1))] : -1;
+      nq[u] = valid ? qual[e] : 0;
+    }
+  };
+  const int64_t gstep = (int64_t)gridDim.x * EPB;
+  load_ids((int64_t)blockIdx.x * EPB);
+  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < E; e0 += gstep) {
     if (threadIdx.x < EPB) {
       const int64_t e = e0 + threadIdx.x;
       const FF c = ff_split((coef && e < E ? coef[e] : 1.0) * g);
@@ -146,22 +164,20 @@ __global__ void __launch_bounds__(256)
       s_cl[threadIdx.x] = c.lo;
     }
     int32_t gid[PER];
-    double rv[PER];
+    double rv[PER], dv[PER];
     bool on[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const int f = threadIdx.x + 256 * u, slot = f / NN, q = f - slot * NN;
-      const int64_t e = e0 + slot;
-      on[u] = f < EPB * NN && e < E && qual[e];
-      gid[u] = -1;
-      rv[u] = 0.0;
-      FF x{0.f, 0.f};
-      if (on[u]) {
-        const int a = q % NI, b = (q / NI) % NI, c = q / (NI * NI);
-        gid[u] = ids[e * Np + (a + 1) + Nq * ((b + 1) + Nq * (c + 1))];
-        rv[u] = r[gid[u]];
-        x = ff_split(k ? rv[u] * down : rv[u]);
-      }
+      on[u] = nq[u] && nid[u] >= 0;
+      gid[u] = nid[u];
+      rv[u] = on[u] ? r[gid[u]] : 0.0;
+      dv[u] = on[u] ? dinv[gid[u]] : 0.0;
+    }
+    if (e0 + gstep < E) load_ids(e0 + gstep);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int f = threadIdx.x + 256 * u;
+      const FF x = on[u] ? ff_split(k ? rv[u] * down : rv[u]) : FF{0.f, 0.f};
       if (f < EPB * NN) {
         s_ah[f] = x.hi;
         s_al[f] = x.lo;
@@ -215,7 +231,7 @@ __global__ void __launch_bounds__(256)
       double zv = ff_widen(s_ah[f]) + ff_widen(s_al[f]);
       if (k) zv = zv * up;
       z[gid[u]] = zv;
-      acc = fma(rv[u], fma(-dinv[gid[u]], rv[u], zv), acc);
+      acc = fma(rv[u], fma(-dv[u], rv[u], zv), acc);
     }
     __syncthreads();
   }
