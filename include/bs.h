@@ -54,6 +54,23 @@ const char *bs_last_error(void);
 /* Library version as 10000*major + 100*minor + patch. */
 int bs_version(void);
 
+/* Checked build (the library compiled with -DBS_CHECK=1; no counterpart in
+ * the paper: a stand-in for a memory checker).  Every kernel then tests each
+ * index it reads from memory -- map entries against N_G, CSR row bounds and
+ * columns against nnz and N_L, gather tiles, the pipelined gather's chunk
+ * ids and staged offsets, the batched solver's items -- before using it; a
+ * failing test records a code (BS_CHK_* in the library's csrc/bs_check_pred.h)
+ * and skips the access (a load reads 0, a store is dropped), so results are
+ * then meaningless but no memory outside the buffers is touched.
+ * bs_check_enabled: 1 in a checked build, 0 otherwise.
+ * bs_check_device: synchronises the current device, collects and clears the
+ * recorded codes; BS_OK when none was recorded (always, in the default
+ * build), BS_ERR_DEVICE_CHECK naming the first code otherwise, BS_ERR_CUDA
+ * when the device cannot be read.  Call it between library calls, not while
+ * another thread is inside one. */
+int bs_check_enabled(void);
+int bs_check_device(void);
+
 /* ------------------------------------------------------------ workspace */
 
 /* Scratch for single-launch reductions: per-block partial sums, an arrival
@@ -233,7 +250,8 @@ int bs_diag_A(const bs_problem *prob, double *d_diag, void *stream);
 int bs_apply_A_ff(const bs_problem *prob, const double *p, double *Ap, void *stream);
 
 /* How A p is formed, process-wide, by bs_apply_A, bs_apply_local,
- * bs_apply_A_ff and every solver but the batched one; mode is a set of bits
+ * bs_apply_A_ff and every solver (the batched one reads BS_OP_DIRECT when a
+ * batch is set up, and never fuses); mode is a set of bits
  * (0, the default, is the fastest measured form):
  *  BS_OP_FUSED: a global node with a single local copy (an element
  *   interior, a face on the natural boundary) needs no gather, so the

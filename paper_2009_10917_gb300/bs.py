@@ -71,6 +71,8 @@ _SIGS = {
     "bs_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "bs_last_error": (ctypes.c_char_p, []),
     "bs_version": (ctypes.c_int, []),
+    "bs_check_enabled": (ctypes.c_int, []),
+    "bs_check_device": (ctypes.c_int, []),
     "bs_workspace_create": (ctypes.c_int, [_pp]),
     "bs_workspace_destroy": (ctypes.c_int, [_vp]),
     "bs_copy": (ctypes.c_int, [_i64, _vp, _vp, _vp]),
@@ -126,8 +128,30 @@ def operator_fusion(on=-1):
     return 1 if prev & BS_OP_FUSED else 0
 
 
+def checked() -> bool:
+    """True when the environment sets BS_CHECK (not 0): the checked build
+    (-DBS_CHECK=1, every index read from memory tested on the device) is
+    loaded, and every call is followed by bs_check_device."""
+    return os.environ.get("BS_CHECK", "0") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(check=checked())
+
+
+# entry points that touch no device state (no check after them)
+_NO_DEVICE = {"bs_error_string", "bs_last_error", "bs_version", "bs_check_enabled",
+              "bs_check_device"}
+
+
+def _device_check(result, func, args):
+    """ctypes errcheck of the checked build: collect the device-side check
+    words after the call and raise on a recorded failure."""
+    rc = _lib.bs_check_device()
+    if rc != BS_OK:
+        raise BSError(rc, func.__name__ + " (device check)",
+                      _lib.bs_last_error().decode(errors="replace"))
+    return result
 
 
 def lib():
@@ -135,18 +159,26 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if _build.is_stale():
+            chk = checked()
+            path = _build.lib_path(check=chk)
+            if _build.is_stale(check=chk):
                 try:
-                    path = _build.build()
+                    path = _build.build(check=chk)
                 except Exception as exc:  # no nvcc or failed build: no fallback
                     if not os.path.exists(path):
-                        raise RuntimeError(f"libbs.so is missing and cannot be built: {exc}")
+                        raise RuntimeError(f"{path} is missing and cannot be built: {exc}")
             L = ctypes.CDLL(path)
             for name, (res, args) in _SIGS.items():
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
+            if bool(L.bs_check_enabled()) != chk:
+                raise RuntimeError(f"{path}: checked build {bool(L.bs_check_enabled())}, "
+                                   f"wanted {chk}")
+            if chk:
+                for name in _SIGS:
+                    if name not in _NO_DEVICE:
+                        getattr(L, name).errcheck = _device_check
             _lib = L
     return _lib
 

@@ -6,7 +6,8 @@ links the shared library.  Flags:
   --fmad=false                              no implicit contraction: every
                                             fused multiply-add is explicit
   -cudart shared                            share the process's CUDA runtime
-Output: paper_2009_10917_gb300/_build/libbs.so
+Output: paper_2009_10917_gb300/_build/libbs.so; with --check (-DBS_CHECK=1,
+device-side index checks) paper_2009_10917_gb300/_build_check/libbs.so.
 """
 from __future__ import annotations
 
@@ -23,6 +24,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libbs.so")
+# the checked build (-DBS_CHECK=1: device-side index checks)
+BUILD_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(BUILD_CHECK, "libbs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
@@ -42,6 +46,7 @@ def _sources():
 
 def _deps():
     return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh"))
+            + glob.glob(os.path.join(CSRC, "*.h"))
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__])
 
 
@@ -68,24 +73,33 @@ def source_digest(names=None) -> str:
     return h.hexdigest()[:16]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def lib_path(check: bool = False) -> str:
+    return LIB_CHECK if check else LIB
+
+
+def is_stale(check: bool = False) -> bool:
+    lib = lib_path(check)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile (if stale) and return the path of libbs.so."""
-    if not force and not is_stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=None,
+          check: bool = False) -> str:
+    """Compile (if stale) and return the path of libbs.so; check=True builds
+    the checked variant (-DBS_CHECK=1) into its own folder."""
+    lib = lib_path(check)
+    if not force and not is_stale(check):
+        return lib
+    out = BUILD_CHECK if check else BUILD
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + (["-DBS_CHECK=1"] if check else []) + list(extra_flags or [])
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         cmd = [cc] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -97,16 +111,17 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None,
+                check="--check" in sys.argv))

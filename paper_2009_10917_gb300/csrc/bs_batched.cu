@@ -43,8 +43,10 @@ __device__ long long g_barrier_budget = kBarrierBudget;
 
 struct BDesc {
   int NQ;
+  int eo;      // 1: even-odd element operator for even NQ (bs_operator_mode at setup)
   int active;  // 1: participates in the current inner/outer step
   int64_t E, NG;
+  int64_t NL, nnz, ntiles;  // bounds of the checked build's index tests
   const int32_t *ids, *order, *row_starts, *col_ids;
   const int2 *tiles;
   const double *coef;
@@ -132,6 +134,24 @@ __device__ __noinline__ void ax_call(int64_t slot0, int64_t E, const int32_t *or
                                 s_w);
 }
 
+// The FP64 even-odd element operator on elements [slot0, slot1): calls of
+// EoShape<NQ, kBBlock>::EPB elements (the whole item: 256 / Nq^2 elements,
+// every thread one (i, j) column).  The float-float and FP32 forms keep the
+// direct element operator here: the even-odd group needs four times the
+// direct form's shared memory (64 KB per block at Nq = 8), and with it the
+// float-float batch (three blocks per SM) took 16.9 s instead of 15.7 s and
+// the FP32 batch 16.4 s instead of 15.6 s, while the FP64 batch gained
+// (28.6 s against 29.1 s).
+template <int NQ>
+__device__ __noinline__ void ax_call_eo(int64_t slot0, int64_t slot1, const int32_t *order,
+                                        const int32_t *ids, const double *in, double *out,
+                                        const OpTab<double> *tab, const double *coef, double g,
+                                        double mlam, double *smem) {
+  for (int64_t s0 = slot0; s0 < slot1; s0 += EoShape<NQ, kBBlock>::EPB)
+    ax_elements_eo<double, NQ, true, false, kBBlock>(s0, slot1, order, ids, in, out, tab, coef,
+                                                     g, mlam, smem, nullptr, nullptr);
+}
+
 // The float-float element operator (bs_op_ff.cuh) as a real call.
 template <int NQ>
 __device__ __noinline__ void ax_call_ff(int64_t slot0, int64_t E, const int32_t *order,
@@ -148,6 +168,21 @@ __device__ __noinline__ void ax_call_ff(int64_t slot0, int64_t E, const int32_t 
 // the float-float operator (FP64 form only).
 template <typename T, bool GATHER_IN, bool FF = false>
 __device__ void item_ax(const BDesc &d, int64_t slot0, const T *in, T *out, T *smem) {
+  // elements of this item: [slot0, slot1)
+  const int nq2 = d.NQ * d.NQ;
+  const int64_t slot1 = slot0 + (nq2 >= 128 ? 1 : 256 / nq2) < d.E
+                            ? slot0 + (nq2 >= 128 ? 1 : 256 / nq2)
+                            : d.E;
+  if constexpr (GATHER_IN && !FF && sizeof(T) == 8) {
+    if (d.eo && (d.NQ == 2 || d.NQ == 4 || d.NQ == 6 || d.NQ == 8)) {
+#define BS_EO_CASE(NQ)                                                                         \
+  case NQ:                                                                                     \
+    ax_call_eo<NQ>(slot0, slot1, d.order, d.ids, in, out, d.tab, d.coef, d.g, d.mlam, smem);   \
+    return;
+      switch (d.NQ) { BS_EO_CASE(2) BS_EO_CASE(4) BS_EO_CASE(6) BS_EO_CASE(8) default: return; }
+#undef BS_EO_CASE
+    }
+  }
   if constexpr (FF) {
     static_assert(sizeof(T) == 8 && GATHER_IN, "float-float operator: FP64 form only");
     {
@@ -227,6 +262,7 @@ __device__ bool item_done(double part, double *parts, int item, int first, int l
 
 struct BLists {
   const BDesc *d;
+  int ns;                     // solves in d
   int chunk;                  // vector entries per C/D item
   const int2 *iA, *iB, *iC;
   int nA, nB, nC;
@@ -266,8 +302,23 @@ __device__ void finish_iteration(const BLists &L, int s, CgState *st, double rr_
 // Shared memory of the element phase, in T: the element values, K and w
 // (FP64 / FP32 operator), or, viewed as floats, the float pairs of the
 // values, the four split tables and the split weights (float-float
-// operator).
-constexpr int kBSmemD = kBSmem + 2 * kBMaxNq * kBMaxNq + 32;
+// operator); in the FP64 form also the largest even-odd element group at
+// this block width (Nq = 8: four elements of 4 x 512 values plus tables).
+// Dynamic: 64 KB in the FP64 form, 19 KB float-float, 9 KB FP32.
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int kBSmemDirect = kBSmem + 2 * kBMaxNq * kBMaxNq + 32;  // doubles
+constexpr int kBSmemD =
+    cmax(kBSmemDirect, cmax(cmax(EoShape<2, kBBlock>::SMEM, EoShape<4, kBBlock>::SMEM),
+                            cmax(EoShape<6, kBBlock>::SMEM, EoShape<8, kBBlock>::SMEM)));
+constexpr int kBSmemF = kBSmem + kBMaxNq * kBMaxNq + 16;  // floats
+template <typename T, bool FF>
+constexpr int iter_smem_bytes() {
+  return sizeof(T) == 8 ? (FF ? kBSmemDirect * 8 : kBSmemD * 8) : kBSmemF * 4;
+}
+static int iter_smem(bool f32, bool ff) {
+  return f32 ? iter_smem_bytes<float, false>()
+             : (ff ? iter_smem_bytes<double, true>() : iter_smem_bytes<double, false>());
+}
 
 // One CG iteration of every running solve (cooperative launch).  U: vector
 // entries per thread per sweep in the update phases (a tuning parameter);
@@ -276,11 +327,13 @@ constexpr int kBSmemD = kBSmem + 2 * kBMaxNq * kBMaxNq + 32;
 template <typename T, int U, bool FF>
 __global__ void __launch_bounds__(kBBlock, FF ? 3 : (sizeof(T) == 8 ? 2 : 4))
     k_batched_iter(BLists L) {
-  __shared__ __align__(16) T smem[sizeof(T) == 8 ? kBSmemD : kBSmem + kBMaxNq * kBMaxNq + 16];
+  extern __shared__ __align__(16) unsigned char bi_smem[];
+  T *smem = reinterpret_cast<T *>(bi_smem);
   if (*(volatile int *)L.err) return;
   // A: ApL = A_L (Z p)
   for (int it = blockIdx.x; it < L.nA; it += gridDim.x) {
     const int2 w = L.iA[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     if (solve_off(d)) continue;
     item_ax<T, true, FF>(d, w.y, BV<T>::p(d), BV<T>::ApL(d), smem);
@@ -289,12 +342,15 @@ __global__ void __launch_bounds__(kBBlock, FF ? 3 : (sizeof(T) == 8 ? 2 : 4))
   // B: Ap = Z^T ApL; p.Ap -> alpha
   for (int it = blockIdx.x; it < L.nB; it += gridDim.x) {
     const int2 w = L.iB[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     if (solve_off(d)) continue;
     Acc<T> acc;
     __syncthreads();
-    gather_tile<T, true, false>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts, d.col_ids, nullptr,
-                                BV<T>::ApL(d), BV<T>::Ap(d), BV<T>::p(d), smem, acc);
+    if (chk(w.y < d.ntiles, BS_CHK_BATCH))
+      gather_tile<T, true, false>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts, d.col_ids,
+                                  nullptr, BV<T>::ApL(d), BV<T>::Ap(d), BV<T>::p(d), smem, acc,
+                                  GBounds{d.NG, d.nnz, d.NL, d.NG});
     const double part = block_sum<kBBlock>(acc.value());
     double pAp;
     const int4 rg = L.rng[w.x];
@@ -313,6 +369,7 @@ __global__ void __launch_bounds__(kBBlock, FF ? 3 : (sizeof(T) == 8 ? 2 : 4))
   // C: x += alpha p; r -= alpha Ap; r.r -> beta, stop flag
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     if (solve_off(d)) continue;
     const T a = BV<T>::alpha(d.st), na = -a;
@@ -354,6 +411,7 @@ __global__ void __launch_bounds__(kBBlock, FF ? 3 : (sizeof(T) == 8 ? 2 : 4))
   // D: p = r + beta p
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     if (solve_off(d)) continue;
     const T bt = BV<T>::beta(d.st);
@@ -382,6 +440,7 @@ __global__ void __launch_bounds__(kBBlock, FF ? 3 : (sizeof(T) == 8 ? 2 : 4))
 __global__ void __launch_bounds__(kBBlock) k_batched_start(BLists L, double tol2, int maxit) {
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     const int64_t i0 = (int64_t)w.y * L.chunk;
     const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
@@ -415,9 +474,11 @@ __global__ void __launch_bounds__(kBBlock) k_batched_start(BLists L, double tol2
 // Refined form, FP64 outer residual, phase 1: ApL = A_L (Z x) for solves
 // that have not converged (x64 through the map, FP64 element operator).
 __global__ void __launch_bounds__(kBBlock) k_batched_outer_ax(BLists L) {
-  __shared__ __align__(16) double smem[kBSmemD];
+  extern __shared__ __align__(16) unsigned char bo_smem[];  // iter_smem_bytes<double, false>()
+  double *smem = reinterpret_cast<double *>(bo_smem);
   for (int it = blockIdx.x; it < L.nA; it += gridDim.x) {
     const int2 w = L.iA[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     if (d.outer_done) continue;
     item_ax<double, true>(d, w.y, d.x, d.ApL, smem);
@@ -429,12 +490,15 @@ __global__ void __launch_bounds__(kBBlock) k_batched_outer_gather(BLists L) {
   __shared__ __align__(16) double smem[kTileNnz];
   for (int it = blockIdx.x; it < L.nB; it += gridDim.x) {
     const int2 w = L.iB[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     if (d.outer_done) continue;
     Acc<double> acc;
     __syncthreads();
-    gather_tile<double, false, false>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts, d.col_ids,
-                                      nullptr, d.ApL, d.Ap, nullptr, smem, acc);
+    if (chk(w.y < d.ntiles, BS_CHK_BATCH))
+      gather_tile<double, false, false>(d.tiles[w.y], d.tiles[w.y + 1], d.row_starts,
+                                        d.col_ids, nullptr, d.ApL, d.Ap, nullptr, smem, acc,
+                                        GBounds{d.NG, d.nnz, d.NL, d.NG});
   }
 }
 
@@ -445,6 +509,7 @@ __global__ void __launch_bounds__(kBBlock)
                              int outer_maxit) {
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     BDesc &d = D[w.x];
     if (d.outer_done) continue;
     const int64_t i0 = (int64_t)w.y * L.chunk;
@@ -493,6 +558,7 @@ __global__ void __launch_bounds__(kBBlock)
 __global__ void __launch_bounds__(kBBlock) k_batched_outer_update(BDesc *D, BLists L) {
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     BDesc &d = D[w.x];
     if (!d.active) continue;
     const int64_t i0 = (int64_t)w.y * L.chunk;
@@ -508,6 +574,7 @@ __global__ void __launch_bounds__(kBBlock) k_batched_outer_update(BDesc *D, BLis
 __global__ void k_batched_zero_x(BLists L) {
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     const BDesc &d = L.d[w.x];
     const int64_t i0 = (int64_t)w.y * L.chunk;
     const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
@@ -519,6 +586,7 @@ __global__ void k_batched_zero_x(BLists L) {
 __global__ void __launch_bounds__(kBBlock) k_batched_bb(BDesc *D, BLists L) {
   for (int it = blockIdx.x; it < L.nC; it += gridDim.x) {
     const int2 w = L.iC[it];
+    if (!chk(bs_pred_index(w.x, L.ns) && w.y >= 0, BS_CHK_BATCH)) continue;
     BDesc &d = D[w.x];
     const int64_t i0 = (int64_t)w.y * L.chunk;
     const int64_t i1 = i0 + L.chunk < d.NG ? i0 + L.chunk : d.NG;
@@ -629,9 +697,13 @@ static int build_batch(Batch &B, int ns, const bs_problem *const *P, const doubl
     BDesc &d = desc[(size_t)s];
     memset(&d, 0, sizeof(d));
     d.NQ = p->N + 1;
+    d.eo = g_op_evenodd;
     d.active = 1;
     d.E = m->E;
     d.NG = m->NG;
+    d.NL = m->NL;
+    d.nnz = m->nnz;
+    d.ntiles = m->ntiles;
     d.ids = m->d_ids;
     d.order = m->d_elem_order;
     d.row_starts = m->d_row_starts;
@@ -683,6 +755,7 @@ static int build_batch(Batch &B, int ns, const bs_problem *const *P, const doubl
   BS_CUDA_TRY(cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking));
   BLists &L = B.L;
   L.d = B.d_desc;
+  L.ns = ns;
   L.chunk = B.chunk;
   L.iA = B.d_items;
   L.iB = B.d_items + B.capA;
@@ -725,7 +798,8 @@ static int launch_iter(Batch &B, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)B.grid_iter);
   cfg.blockDim = dim3(kBBlock);
-  cfg.dynamicSmemBytes = 0;
+  const int smem = iter_smem(sizeof(T) == 4, B.ff);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -733,7 +807,10 @@ static int launch_iter(Batch &B, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void *args[] = {&B.L};
-  BS_CUDA_TRY(cudaLaunchKernelExC(&cfg, iter_kernel<T>(B.unroll, B.ff), args));
+  const void *kern = iter_kernel<T>(B.unroll, B.ff);
+  if (occupancy_blocks_smem(kern, kBBlock, smem) < 1)  // sets the smem limit
+    return fail(BS_ERR_CUDA, "batched CG: shared memory refused");
+  BS_CUDA_TRY(cudaLaunchKernelExC(&cfg, kern, args));
   return BS_OK;
 }
 
@@ -783,14 +860,12 @@ static int iterate(Batch &B, bool graph, int maxit, cudaStream_t s) {
 }
 
 // Cooperative grid: SMs x blocks per SM, the occupancy maximum or fewer
-// (want > 0).
-static int occupancy_grid(const void *kern, int want = 0) {
+// (want > 0), at `smem` bytes of dynamic shared memory per block.
+static int occupancy_grid(const void *kern, int smem, int want = 0) {
   DeviceInfo di;
   if (device_info(&di)) return 0;
-  int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kBBlock, 0) != cudaSuccess ||
-      bps < 1)
-    return 0;
+  int bps = occupancy_blocks_smem(kern, kBBlock, smem);
+  if (bps < 1) return 0;
   if (want > 0 && want < bps) bps = want;
   return bps * di.sms;
 }
@@ -848,6 +923,7 @@ static int setup_batch(Batch &B, int32_t nsolves, const bs_problem *const *probs
   if (int rc = build_batch(B, nsolves, probs, b, x, f32)) return rc;
   B.grid_iter = occupancy_grid(f32 ? iter_kernel<float>(B.unroll)
                                    : iter_kernel<double>(B.unroll, B.ff),
+                               iter_smem(f32, B.ff),
                                cfg ? cfg->blocks_per_sm : 0);
   if (B.grid_iter < 1) return fail(BS_ERR_CUDA, "batched CG: no cooperative grid");
   return BS_OK;
@@ -867,7 +943,9 @@ static int solve_batched(int32_t nsolves, const bs_problem *const *probs, const 
   if (rc) return rc;
   const bool graph = flags & BS_CG_GRAPH;
   const int G = stream_grid((int64_t)B.capC, 1, 1, 8);
-  const int GA = occupancy_grid((const void *)k_batched_outer_ax);
+  const int GA =
+      occupancy_grid((const void *)k_batched_outer_ax, iter_smem_bytes<double, false>());
+  if (GA < 1) return fail(BS_ERR_CUDA, "batched CG: no grid for the outer residual");
   if (!f32) {
     k_batched_start<<<G, kBBlock, 0, s>>>(B.L, tol * tol, maxit);
     BS_LAUNCH_CHECK();
@@ -889,7 +967,7 @@ static int solve_batched(int32_t nsolves, const bs_problem *const *probs, const 
         if ((rc = upload_lists(B, open, s))) break;
       }
       BS_CUDA_TRY(cudaMemsetAsync(B.L.active, 0, sizeof(int), s));
-      k_batched_outer_ax<<<GA > 0 ? GA : G, kBBlock, 0, s>>>(B.L);
+      k_batched_outer_ax<<<GA, kBBlock, iter_smem_bytes<double, false>(), s>>>(B.L);
       k_batched_outer_gather<<<G, kBBlock, 0, s>>>(B.L);
       k_batched_outer_residual<<<G, kBBlock, 0, s>>>(B.d_desc, B.L, tol * tol, itol * itol,
                                                       maxit, outer_maxit);
@@ -988,8 +1066,13 @@ static int autotune(int32_t nsolves, const bs_problem *const *probs, const doubl
           // the first inner solve of the refined form: r = b (x = 0)
           k_batched_zero_x<<<G, kBBlock, 0, s>>>(B.L);
           k_batched_bb<<<G, kBBlock, 0, s>>>(B.d_desc, B.L);
-          const int GA = occupancy_grid((const void *)k_batched_outer_ax);
-          k_batched_outer_ax<<<GA > 0 ? GA : G, kBBlock, 0, s>>>(B.L);
+          const int GA =
+              occupancy_grid((const void *)k_batched_outer_ax, iter_smem_bytes<double, false>());
+          if (GA < 1) {
+            rc = fail(BS_ERR_CUDA, "bs_cg_batched_autotune: no grid for the outer residual");
+            break;
+          }
+          k_batched_outer_ax<<<GA, kBBlock, iter_smem_bytes<double, false>(), s>>>(B.L);
           k_batched_outer_gather<<<G, kBBlock, 0, s>>>(B.L);
           k_batched_outer_residual<<<G, kBBlock, 0, s>>>(B.d_desc, B.L, 0.0, 0.0, 1 << 30, 50);
         }

@@ -87,7 +87,7 @@ inline void sym_eig(int n, double *A, double *Q, double *lam) {
 // qual[e] = 1 when every interior node of element e is unmasked and has no
 // other copy (valence 1): only then is the element's interior block a
 // diagonal block of A.
-__global__ void k_bj_qualify(int64_t E, int N, const int32_t *__restrict__ ids,
+__global__ void k_bj_qualify(int64_t E, int64_t NG, int N, const int32_t *__restrict__ ids,
                              const int32_t *__restrict__ row_starts, uint8_t *__restrict__ qual) {
   const int Nq = N + 1, Np = Nq * Nq * Nq;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -97,6 +97,10 @@ __global__ void k_bj_qualify(int64_t E, int N, const int32_t *__restrict__ ids,
       for (int j = 1; j < N && ok; ++j)
         for (int i = 1; i < N && ok; ++i) {
           const int32_t g = ids[e * Np + i + Nq * (j + Nq * k)];
+          if (!chk(bs_pred_map_entry(g, NG), BS_CHK_PREC_ENTRY)) {
+            ok = 0;
+            break;
+          }
           ok = g >= 0 && row_starts[g + 1] - row_starts[g] == 1;
         }
     qual[e] = ok;
@@ -151,6 +155,7 @@ __global__ void __launch_bounds__(256)
       const bool valid = f < EPB * NN && e < E;
       const int a = q % NI, b = (q / NI) % NI, c = q / (NI * NI);
       nid[u] = valid ? ids[e * Np + (a + 1) + Nq * ((b + 1) + Nq * (c + 1))] : -1;
+      if (!chk(bs_pred_map_entry(nid[u], NG), BS_CHK_PREC_ENTRY)) nid[u] = -1;
       nq[u] = valid ? qual[e] : 0;
     }
   };
@@ -285,7 +290,7 @@ inline int bj_ensure(bs_problem *P, cudaStream_t s) {
   BS_CUDA_TRY(cudaMemcpy(mem, &h, sizeof(h), cudaMemcpyHostToDevice));
   uint8_t *qual = static_cast<uint8_t *>(mem) + kBjQualOffset;
   if (E > 0) {
-    k_bj_qualify<<<stream_grid(E, 1, 256, 4), 256, 0, s>>>(E, N, P->map->d_ids,
+    k_bj_qualify<<<stream_grid(E, 1, 256, 4), 256, 0, s>>>(E, P->map->NG, N, P->map->d_ids,
                                                            P->map->d_row_starts, qual);
     BS_LAUNCH_CHECK();
   }

@@ -172,26 +172,33 @@ static int pcg_update_launch(const bs_problem *P, double *x, int init, cudaStrea
 // ------------------------------------------------------------ scattered storage
 
 // owner[l] = 1 when l is the lowest local copy of its global node.
-__global__ void k_owner(int64_t NL, const int32_t *__restrict__ ids,
+// NG, nnz: bounds of the checked build's index tests.
+__global__ void k_owner(int64_t NL, int64_t NG, int64_t nnz, const int32_t *__restrict__ ids,
                         const int32_t *__restrict__ rs, const int32_t *__restrict__ cols,
                         uint8_t *__restrict__ owner) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   for (int64_t l = tid; l < NL; l += nth) {
-    const int32_t id = ids[l];
+    int32_t id = ids[l];
+    if (!chk(bs_pred_map_entry(id, NG), BS_CHK_SCATTER_ENTRY) ||
+        (id >= 0 && !chk(bs_pred_index(rs[id], nnz), BS_CHK_GATHER_ROW)))
+      id = -1;
     owner[l] = id >= 0 && cols[rs[id]] == (int32_t)l ? 1 : 0;
   }
 }
 
 // xG[g] = xL at the lowest copy of g (0 for a node without copies).
-__global__ void k_extract(int64_t NG, const int32_t *__restrict__ rs,
+__global__ void k_extract(int64_t NG, int64_t NL, int64_t nnz, const int32_t *__restrict__ rs,
                           const int32_t *__restrict__ cols, const double *__restrict__ xL,
                           double *__restrict__ xG) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = tid; g < NG; g += nth) {
     const int32_t a = rs[g];
-    xG[g] = a < rs[g + 1] ? xL[cols[a]] : 0.0;
+    bool ok = a < rs[g + 1];
+    if (ok && !chk(bs_pred_index(a, nnz) && bs_pred_index(cols[a], NL), BS_CHK_GATHER_COL))
+      ok = false;
+    xG[g] = ok ? xL[cols[a]] : 0.0;
   }
 }
 
@@ -201,7 +208,8 @@ __global__ void k_extract(int64_t NG, const int32_t *__restrict__ rs,
 // one by the first thread.
 template <class Ep>
 __global__ void __launch_bounds__(kReduceBlock)
-    k_scatter_dot(int64_t NL, const int32_t *__restrict__ ids, const uint8_t *__restrict__ owner,
+    k_scatter_dot(int64_t NL, int64_t NG, const int32_t *__restrict__ ids,
+                  const uint8_t *__restrict__ owner,
                   const double *__restrict__ qG, double *__restrict__ qL,
                   const double *__restrict__ w, double *partials, unsigned int *counter, Ep ep,
                   const CgState *st) {
@@ -211,7 +219,9 @@ __global__ void __launch_bounds__(kReduceBlock)
   double acc = 0.0;
   const int64_t npair = NL / 2;
   for (int64_t q = tid; q < npair; q += nth) {
-    const int2 id = __ldcs(reinterpret_cast<const int2 *>(ids) + q);
+    int2 id = __ldcs(reinterpret_cast<const int2 *>(ids) + q);
+    if (!chk(bs_pred_map_entry(id.x, NG), BS_CHK_SCATTER_ENTRY)) id.x = -1;
+    if (!chk(bs_pred_map_entry(id.y, NG), BS_CHK_SCATTER_ENTRY)) id.y = -1;
     const uchar2 o = __ldcs(reinterpret_cast<const uchar2 *>(owner) + q);
     // a masked entry keeps its value: read the pair only when there is one
     double2 v = (id.x < 0 || id.y < 0) ? __ldcs(reinterpret_cast<const double2 *>(qL) + q)
@@ -227,7 +237,8 @@ __global__ void __launch_bounds__(kReduceBlock)
   }
   if ((NL & 1) && tid == 0) {
     const int64_t l = NL - 1;
-    const int32_t id = ids[l];
+    int32_t id = ids[l];
+    if (!chk(bs_pred_map_entry(id, NG), BS_CHK_SCATTER_ENTRY)) id = -1;
     if (id >= 0) {
       const double v = qG[id];
       qL[l] = v;
@@ -346,7 +357,7 @@ static int ensure_scattered(bs_problem *P, cudaStream_t s) {
   }
   if (m->NL > 0) {
     k_owner<<<stream_grid(m->NL, 1, kStreamBlock, 8), kStreamBlock, 0, s>>>(
-        m->NL, m->d_ids, m->d_row_starts, m->d_col_ids, P->d_owner);
+        m->NL, m->NG, m->nnz, m->d_ids, m->d_row_starts, m->d_col_ids, P->d_owner);
     BS_LAUNCH_CHECK();
   }
   return BS_OK;
@@ -391,7 +402,7 @@ static int scat_iteration(const bs_problem *P, bool precond, bool ff, cudaStream
     auto kern = k_scatter_dot<EpAlpha>;
     int grid = stream_grid(m->NL / 2 + 1, 1, kReduceBlock, blocks_per_sm(kern, kReduceBlock));
     if (grid > kMaxPartials) grid = kMaxPartials;
-    kern<<<grid, kReduceBlock, 0, s>>>(m->NL, m->d_ids, P->d_owner, v.Ap, L.Ap, L.p,
+    kern<<<grid, kReduceBlock, 0, s>>>(m->NL, m->NG, m->d_ids, P->d_owner, v.Ap, L.Ap, L.p,
                                        P->d_partials, P->d_counter,
                                        EpAlpha{st, precond ? 1 : 0}, st);
     BS_LAUNCH_CHECK();
@@ -587,7 +598,7 @@ extern "C" int bs_cg_solve(const bs_problem *Pc, const double *b, double *x, dou
     }
     if (scat && NG > 0) {  // x_G from the lowest copy of each node
       k_extract<<<stream_grid(NG, 1, kStreamBlock, 8), kStreamBlock, 0, s>>>(
-          NG, m->d_row_starts, m->d_col_ids, lvecs(P).x, x);
+          NG, m->NL, m->nnz, m->d_row_starts, m->d_col_ids, lvecs(P).x, x);
       BS_CUDA_TRY(cudaGetLastError());
     }
     BS_CUDA_TRY(cudaMemcpyAsync(P->h_state, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));

@@ -5,6 +5,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "bs_internal.cuh"
 
@@ -67,6 +68,54 @@ int occupancy_blocks(const void *kernel, int block) {
   return b;
 }
 
+// The check-word readers of all translation units (checked build; empty in
+// the default build).
+static std::mutex g_check_mu;
+static std::vector<int (*)(unsigned int *)> &check_readers() {
+  static std::vector<int (*)(unsigned int *)> v;
+  return v;
+}
+
+int register_check_word(int (*read_and_clear)(unsigned int *)) {
+  std::lock_guard<std::mutex> lock(g_check_mu);
+  check_readers().push_back(read_and_clear);
+  return (int)check_readers().size();
+}
+
+static const char *check_code_name(unsigned int code) {
+  switch (code) {
+    case BS_CHK_SCATTER_ENTRY: return "scatter: map entry >= N_G";
+    case BS_CHK_GATHER_TILE: return "gather: tile bounds outside the CSR";
+    case BS_CHK_GATHER_ROW: return "gather: row bounds outside [0, nnz]";
+    case BS_CHK_GATHER_COL: return "gather: column >= N_L";
+    case BS_CHK_GATHER_CHUNK: return "pipelined gather: chunk id outside q_L";
+    case BS_CHK_GATHER_STAGED: return "pipelined gather: offset outside the staged tile";
+    case BS_CHK_OP_ENTRY: return "element operator: map entry out of range";
+    case BS_CHK_PREC_ENTRY: return "preconditioner or network epilogue: map entry out of range";
+    case BS_CHK_ROWS: return "multi-rank rows: index out of range";
+    case BS_CHK_BATCH: return "batched solver: index out of range";
+    default: return "unknown check";
+  }
+}
+
+int occupancy_blocks_smem(const void *kernel, int block, int smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void *, int, int, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_tuple(kernel, block, smem, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int b = 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, smem) != cudaSuccess)
+    b = 0;
+  cache[key] = b;
+  return b;
+}
+
 }  // namespace bs
 
 extern "C" {
@@ -88,6 +137,28 @@ const char *bs_error_string(int status) {
 const char *bs_last_error(void) { return bs::t_err; }
 
 int bs_version(void) { return 10000; }
+
+int bs_check_enabled(void) { return BS_CHECK ? 1 : 0; }
+
+int bs_check_device(void) {
+  if (!BS_CHECK) return BS_OK;
+  BS_CUDA_TRY(cudaDeviceSynchronize());
+  unsigned int first = 0;
+  int nfail = 0;
+  std::lock_guard<std::mutex> lock(bs::g_check_mu);
+  for (auto rd : bs::check_readers()) {
+    unsigned int w = 0;
+    if (rd(&w) != 0) return bs::fail(BS_ERR_CUDA, "bs_check_device: reading a check word");
+    if (w) {
+      ++nfail;
+      if (!first) first = w;
+    }
+  }
+  if (first)
+    return bs::fail(BS_ERR_DEVICE_CHECK, "device check %u (%s) failed in %d unit(s)", first,
+                    bs::check_code_name(first), nfail);
+  return BS_OK;
+}
 
 int bs_workspace_create(bs_workspace **ws) {
   BS_ARG(ws != nullptr, "bs_workspace_create: ws is NULL");

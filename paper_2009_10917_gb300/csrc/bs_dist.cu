@@ -31,36 +31,45 @@ constexpr int kRowsBlock = 256;
 
 // qG[rows[i]] = (start ? start[i] : +0) + the row's copies in ascending
 // local order, one serial sum per thread.  With start == NULL the first term
-// enters as +0.0 + q (a -0.0 copy becomes +0.0), as in the gather.
+// enters as +0.0 + q (a -0.0 copy becomes +0.0), as in the gather.  gb
+// bounds the indices in the checked build.
 __global__ void __launch_bounds__(kRowsBlock)
-    k_gather_rows(int64_t n, const int32_t *__restrict__ rows,
+    k_gather_rows(int64_t n, GBounds gb, const int32_t *__restrict__ rows,
                   const int32_t *__restrict__ row_starts, const int32_t *__restrict__ col_ids,
                   const double *__restrict__ qL, const double *__restrict__ start,
                   double *__restrict__ qG) {
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nth) {
     const int32_t g = rows[i];
-    const int32_t a = row_starts[g], b = row_starts[g + 1];
+    if (!chk(bs_pred_index(g, gb.ng), BS_CHK_ROWS)) continue;
+    int32_t a = row_starts[g], b = row_starts[g + 1];
+    if (!chk(bs_pred_row(a, b, gb.nnz), BS_CHK_ROWS)) a = b = 0;
     double s;
     int32_t k = a;
     if (start) {
       s = start[i];
     } else {
-      s = a < b ? plus_zero(qL[col_ids[a]]) : 0.0;
+      s = 0.0;
+      if (a < b && chk(bs_pred_index(col_ids[a], gb.nl), BS_CHK_ROWS))
+        s = plus_zero(qL[col_ids[a]]);
       k = a + 1;
     }
-    for (; k < b; ++k) s = s + qL[col_ids[k]];
+    for (; k < b; ++k) {
+      const int32_t c = col_ids[k];
+      if (chk(bs_pred_index(c, gb.nl), BS_CHK_ROWS)) s = s + qL[c];
+    }
     qG[g] = s;
   }
 }
 
-// buf[i] = qG[rows[i]] (PACK) or qG[rows[i]] = buf[i].
+// buf[i] = qG[rows[i]] (PACK) or qG[rows[i]] = buf[i]; ng: length of qG.
 template <bool PACK>
 __global__ void __launch_bounds__(kRowsBlock)
-    k_rows_move(int64_t n, const int32_t *__restrict__ rows, const double *__restrict__ src,
-                double *__restrict__ dst) {
+    k_rows_move(int64_t n, int64_t ng, const int32_t *__restrict__ rows,
+                const double *__restrict__ src, double *__restrict__ dst) {
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nth) {
+    if (!chk(bs_pred_index(rows[i], ng), BS_CHK_ROWS)) continue;
     if (PACK)
       dst[i] = src[rows[i]];
     else
@@ -138,7 +147,8 @@ int bs_gather_rows(const bs_rows *rs, const double *qL, const double *start, dou
   const int grid = rows_grid(rs->n);
   if (grid < 1) return fail(BS_ERR_CUDA, "bs_gather_rows: no device");
   k_gather_rows<<<grid, kRowsBlock, 0, as_stream(stream)>>>(
-      rs->n, rs->d_rows, rs->map->d_row_starts, rs->map->d_col_ids, qL, start, qG);
+      rs->n, GBounds{rs->map->NG, rs->map->nnz, rs->map->NL, rs->map->NG}, rs->d_rows,
+      rs->map->d_row_starts, rs->map->d_col_ids, qL, start, qG);
   BS_LAUNCH_CHECK();
   return BS_OK;
 }
@@ -149,7 +159,8 @@ int bs_rows_pack(const bs_rows *rs, const double *qG, double *buf, void *stream)
   BS_ARG(qG != nullptr && buf != nullptr, "bs_rows_pack: NULL vector");
   const int grid = rows_grid(rs->n);
   if (grid < 1) return fail(BS_ERR_CUDA, "bs_rows_pack: no device");
-  k_rows_move<true><<<grid, kRowsBlock, 0, as_stream(stream)>>>(rs->n, rs->d_rows, qG, buf);
+  k_rows_move<true><<<grid, kRowsBlock, 0, as_stream(stream)>>>(rs->n, rs->map->NG, rs->d_rows,
+                                                                qG, buf);
   BS_LAUNCH_CHECK();
   return BS_OK;
 }
@@ -160,7 +171,8 @@ int bs_rows_unpack(const bs_rows *rs, const double *buf, double *qG, void *strea
   BS_ARG(qG != nullptr && buf != nullptr, "bs_rows_unpack: NULL vector");
   const int grid = rows_grid(rs->n);
   if (grid < 1) return fail(BS_ERR_CUDA, "bs_rows_unpack: no device");
-  k_rows_move<false><<<grid, kRowsBlock, 0, as_stream(stream)>>>(rs->n, rs->d_rows, buf, qG);
+  k_rows_move<false><<<grid, kRowsBlock, 0, as_stream(stream)>>>(rs->n, rs->map->NG, rs->d_rows,
+                                                                 buf, qG);
   BS_LAUNCH_CHECK();
   return BS_OK;
 }

@@ -61,7 +61,8 @@ __device__ __forceinline__ float shifted_hi(double x, int emax) {
 
 template <int NP>
 __global__ void __launch_bounds__(kPrepBlock)
-    k_fp_prep(int64_t E, int Dp, int split, float oscale, const int32_t *__restrict__ order,
+    k_fp_prep(int64_t E, int64_t NG, int Dp, int split, float oscale,
+              const int32_t *__restrict__ order,
               const int32_t *__restrict__ ids, const double *__restrict__ r,
               const double *__restrict__ dinv, __nv_bfloat16 *__restrict__ X,
               double *__restrict__ rmsv, const CgState *st) {
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(kPrepBlock)
   const int64_t q = (int64_t)blockIdx.x * (kPrepBlock / 32) + (threadIdx.x >> 5);
   if (q >= E) return;
   const int64_t e = order[q];
+  if (!chk(bs_pred_index(e, E), BS_CHK_PREC_ENTRY)) return;  // warp-uniform
   const int32_t *id = ids + e * NP;
   // all of a lane's map entries, then all of its gathers, so that the loads
   // of an element are in flight together
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(kPrepBlock)
   for (int t = 0; t < T; ++t) {
     const int l = lane + 32 * t;
     g[t] = l < NP ? __ldcs(id + l) : -1;
+    if (!chk(bs_pred_map_entry(g[t], NG), BS_CHK_PREC_ENTRY)) g[t] = -1;
   }
   double rv[T], dv[T];
 #pragma unroll
@@ -125,14 +128,15 @@ __global__ void __launch_bounds__(kPrepBlock)
   if (lane == 0) rmsv[q] = rms > 0.f ? ldexp((double)(rms * oscale), er + ed - 2046) : 0.0;
 }
 
-static int launch_fp_prep(int N, int64_t E, int Dp, int split, float oscale, const int32_t *order,
+static int launch_fp_prep(int N, int64_t E, int64_t NG, int Dp, int split, float oscale,
+                          const int32_t *order,
                           const int32_t *ids, const double *r, const double *dinv,
                           __nv_bfloat16 *X, double *rmsv, const CgState *st, cudaStream_t s) {
   const unsigned grid = (unsigned)((E + kPrepBlock / 32 - 1) / (kPrepBlock / 32));
 #define BS_PREP_CASE(NQ)                                                                     \
   case NQ:                                                                                   \
-    k_fp_prep<NQ * NQ * NQ><<<grid, kPrepBlock, 0, s>>>(E, Dp, split, oscale, order, ids, r, \
-                                                        dinv, X, rmsv, st);                  \
+    k_fp_prep<NQ * NQ * NQ><<<grid, kPrepBlock, 0, s>>>(E, NG, Dp, split, oscale, order, ids, \
+                                                        r, dinv, X, rmsv, st);               \
     break;
   switch (N + 1) {
     BS_PREP_CASE(3)
@@ -331,8 +335,8 @@ static int precondition(const bs_problem *P, bs_mlp *mlp, int odd, int init, cud
   if (mlp) {
     const int64_t E = m->E;
     double *rmsv = reinterpret_cast<double *>(mlp->Y);  // E doubles of inference scratch
-    if (int rc = launch_fp_prep(P->N, E, mlp->Dp, mlp->split, 1.0f, m->d_elem_order, m->d_ids,
-                                v.r, v.dinv, mlp->Xb, rmsv, st, s))
+    if (int rc = launch_fp_prep(P->N, E, m->NG, mlp->Dp, mlp->split, 1.0f, m->d_elem_order,
+                                m->d_ids, v.r, v.dinv, mlp->Xb, rmsv, st, s))
       return rc;
     GemmArgs b{};
     b.nvalid = mlp->nI;
@@ -342,6 +346,7 @@ static int precondition(const bs_problem *P, bs_mlp *mlp, int odd, int init, cud
     b.order = m->d_elem_order;
     b.lidx = mlp->lidx;
     b.np = Np;
+    b.ng = m->NG;
     b.st = st;
     if (odd) {
       // the odd part W2 W1 x / 2 is linear: one GEMM with the interior rows of
@@ -444,6 +449,7 @@ __global__ void __launch_bounds__(128)
   for (int k = t; k < NQ2; k += blockDim.x) s_K[k] = tab->K[k];
   for (int k = t; k < NQ; k += blockDim.x) s_w[k] = tab->w[k];
   const int32_t e = elems[q];
+  if (!chk(bs_pred_index(e, tab->ne), BS_CHK_PREC_ENTRY)) return;  // block-uniform
   const int32_t *id = ids + (int64_t)e * NP;
   const double c = coef ? coef[e] : 1.0;
   const double sgn = (negate_odd && (q & 1)) ? -1.0 : 1.0;
@@ -456,7 +462,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
       const int l = i + NQ * j + NQ2 * k;
-      const int32_t gI = id[l];
+      int32_t gI = id[l];
+      if (!chk(bs_pred_map_entry(gI, tab->ng), BS_CHK_PREC_ENTRY)) gI = -1;
       const double u = gI >= 0 ? dinv[gI] * r[gI] : 0.0;
       s_u[l] = u;
       ss = fma(u, u, ss);

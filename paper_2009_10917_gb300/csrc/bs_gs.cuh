@@ -34,6 +34,14 @@ struct bs_map {
   int32_t *d_sh_starts;   // [nsh + 1]
   int32_t *d_sh_cols;     // [nnz_sh] the rows' CSR entries, ascending local index
   int2 *d_sh_tiles;       // [nsh_tiles + 1]
+  // The pipelined FP64 gather (bs_gather.cuh, k_gather_async): per tile the
+  // distinct 16-byte chunks of q_L it reads and a blob of uint16 entry offsets
+  // and row starts; NULL when N_L is odd (a chunk would leave q_L).
+  int64_t ag_ntiles;
+  int4 *d_ag_info;        // [ag_ntiles + 1] first row, first chunk, first blob word,
+                          // (entries << 16 | rows), or -1: rows summed straight from the CSR
+  int32_t *d_ag_chunks;   // chunk c covers q_L[2c], q_L[2c + 1]
+  uint4 *d_ag_blob;       // 16-byte words
 };
 
 namespace bs {
@@ -44,10 +52,11 @@ template <> struct Vec2Of<float> { using type = float2; };
 
 constexpr int kScatterBlock = 256;
 
-// qL[l] = qG[ids[l]] for ids[l] >= 0, element by element in `order`.
+// qL[l] = qG[ids[l]] for ids[l] >= 0, element by element in `order`.  NG
+// bounds the map entries in the checked build.
 template <typename T, int U>
 __global__ void __launch_bounds__(kScatterBlock)
-    k_scatter(int64_t E, int Np, const int32_t *__restrict__ order,
+    k_scatter(int64_t E, int64_t NG, int Np, const int32_t *__restrict__ order,
               const int32_t *__restrict__ ids, const T *__restrict__ qG, T *__restrict__ qL) {
   // Np <= 256: EPB elements per group, thread -> (element slot, node) once;
   // Np > 256: one element per group, threads stride over its nodes.
@@ -64,9 +73,13 @@ __global__ void __launch_bounds__(kScatterBlock)
       for (int u = 0; u < U; ++u) {
         const int64_t slot = (g + (int64_t)u * gridDim.x) * epb + sub;
         l[u] = slot < E ? (int64_t)__ldg(order + slot) * Np + node : -1;
+        if (l[u] >= 0 && !chk(bs_pred_index(l[u] / Np, E), BS_CHK_SCATTER_ENTRY)) l[u] = -1;
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) id[u] = l[u] >= 0 ? __ldcs(ids + l[u]) : -1;
+      for (int u = 0; u < U; ++u) {
+        id[u] = l[u] >= 0 ? __ldcs(ids + l[u]) : -1;
+        if (!chk(bs_pred_map_entry(id[u], NG), BS_CHK_SCATTER_ENTRY)) id[u] = -1;
+      }
       T v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) v[u] = id[u] >= 0 ? qG[id[u]] : T(0);
@@ -81,7 +94,7 @@ __global__ void __launch_bounds__(kScatterBlock)
 // every element row and pair is aligned).
 template <typename T, int U>
 __global__ void __launch_bounds__(kScatterBlock)
-    k_scatter2(int64_t E, int Np, const int32_t *__restrict__ order,
+    k_scatter2(int64_t E, int64_t NG, int Np, const int32_t *__restrict__ order,
                const int32_t *__restrict__ ids, const T *__restrict__ qG, T *__restrict__ qL) {
   using V2 = typename Vec2Of<T>::type;
   const int pairs = Np / 2;
@@ -98,10 +111,14 @@ __global__ void __launch_bounds__(kScatterBlock)
       for (int u = 0; u < U; ++u) {
         const int64_t slot = (g + (int64_t)u * gridDim.x) * epb + sub;
         l[u] = slot < E ? (int64_t)__ldg(order + slot) * Np + 2 * pr : -1;
+        if (l[u] >= 0 && !chk(bs_pred_index(l[u] / Np, E), BS_CHK_SCATTER_ENTRY)) l[u] = -1;
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+      for (int u = 0; u < U; ++u) {
         id[u] = l[u] >= 0 ? __ldcs(reinterpret_cast<const int2 *>(ids + l[u])) : make_int2(-1, -1);
+        if (!chk(bs_pred_map_entry(id[u].x, NG), BS_CHK_SCATTER_ENTRY)) id[u].x = -1;
+        if (!chk(bs_pred_map_entry(id[u].y, NG), BS_CHK_SCATTER_ENTRY)) id[u].y = -1;
+      }
       T a[U], b[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -136,7 +153,7 @@ int launch_scatter(const bs_map *m, const T *qG, T *qL, cudaStream_t s) {
     const int64_t groups = (m->E + epb - 1) / epb;
     int grid = stream_grid(groups, U, 1, blocks_per_sm(kern, kScatterBlock));
     if (grid < 1) return fail(BS_ERR_CUDA, "no device");
-    kern<<<grid, kScatterBlock, 0, s>>>(m->E, Np, m->d_elem_order, m->d_ids, qG, qL);
+    kern<<<grid, kScatterBlock, 0, s>>>(m->E, m->NG, Np, m->d_elem_order, m->d_ids, qG, qL);
     BS_LAUNCH_CHECK();
     return BS_OK;
   }
@@ -146,7 +163,7 @@ int launch_scatter(const bs_map *m, const T *qG, T *qL, cudaStream_t s) {
   const int64_t groups = (m->E + epb - 1) / epb;
   int grid = stream_grid(groups, U, 1, blocks_per_sm(kern, kScatterBlock));
   if (grid < 1) return fail(BS_ERR_CUDA, "no device");
-  kern<<<grid, kScatterBlock, 0, s>>>(m->E, Np, m->d_elem_order, m->d_ids, qG, qL);
+  kern<<<grid, kScatterBlock, 0, s>>>(m->E, m->NG, Np, m->d_elem_order, m->d_ids, qG, qL);
   BS_LAUNCH_CHECK();
   return BS_OK;
 }

@@ -12,6 +12,7 @@
 #include <cstdio>
 
 #include "bs.h"
+#include "bs_check.cuh"
 
 namespace bs {
 
@@ -67,6 +68,14 @@ int stream_grid(int64_t work, int per_thread, int block, int blocks_per_sm);
 // Resident blocks per SM of `kernel` at `block` threads on the current
 // device (queried once per kernel and device, then cached).
 int occupancy_blocks(const void *kernel, int block);
+
+// As occupancy_blocks for launches with `smem` bytes of dynamic shared
+// memory; first raises the kernel's dynamic shared-memory limit to `smem`
+// (once per kernel and device).  A kernel template instantiated in several
+// translation units has one host entry per unit, each registered on its own,
+// so the limit is kept per entry address.  Returns 0 when the device refuses
+// the limit or fits no block.
+int occupancy_blocks_smem(const void *kernel, int block, int smem);
 
 }  // namespace bs
 

@@ -115,7 +115,10 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_tn(GemmArgs g) {
       const int64_t m = m0 + wm * TM + mt * 16 + gq + 8 * h;
       if (m >= g.M) continue;
       const int32_t *idrow = nullptr;
-      if (EPI == EPI_SCATTER_F64) idrow = g.ids + (int64_t)(g.order ? g.order[m] : m) * g.np;
+      if (EPI == EPI_SCATTER_F64) {
+        const int64_t em = g.order ? g.order[m] : m;
+        idrow = chk(bs_pred_index(em, g.M), BS_CHK_PREC_ENTRY) ? g.ids + em * g.np : nullptr;
+      }
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const int n = n0 + wn * TN + nt * 8 + 2 * tq;
@@ -324,13 +327,15 @@ __global__ void k_odd_matrix(int H, int Dp, int split, const float *__restrict__
   }
 }
 
-// out rows n < nI: row lidx[n] of src (row length K, both operands).
-__global__ void k_rows(int nI, int K, const int32_t *__restrict__ lidx,
+// out rows n < nI: row lidx[n] of src (row length K, both operands; src
+// has nsrc rows).
+__global__ void k_rows(int nI, int K, int nsrc, const int32_t *__restrict__ lidx,
                        const __nv_bfloat16 *__restrict__ src, __nv_bfloat16 *__restrict__ out) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < (int64_t)nI * K; i += nth) {
     const int64_t n = i / K, k = i - n * K;
+    if (!chk(bs_pred_index(lidx[n], nsrc), BS_CHK_PREC_ENTRY)) continue;
     out[i] = src[(int64_t)lidx[n] * K + k];
   }
 }
@@ -341,8 +346,8 @@ int mlp_interior_operand(bs_mlp *m, int odd, cudaStream_t s) {
   if (odd)
     if (int rc = mlp_odd_matrix(m, s)) return rc;
   const int K = odd ? (m->split ? 3 * m->Dp : m->Dp) : (m->split ? 3 * m->H : m->H);
-  k_rows<<<stream_grid((int64_t)m->nI * K, 1, 256, 8), 256, 0, s>>>(m->nI, K, m->lidx,
-                                                                    odd ? m->Lb : m->W2b, m->Wint);
+  k_rows<<<stream_grid((int64_t)m->nI * K, 1, 256, 8), 256, 0, s>>>(
+      m->nI, K, m->Dp, m->lidx, odd ? m->Lb : m->W2b, m->Wint);
   BS_LAUNCH_CHECK();
   m->int_step = m->step;
   m->int_odd = odd;

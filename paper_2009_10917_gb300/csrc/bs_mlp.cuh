@@ -87,6 +87,7 @@ struct GemmArgs {
   const double *scale;  // EPI_SCALE_F64 / EPI_SCATTER_F64: per-row factor
   const int32_t *ids, *order, *lidx;  // EPI_SCATTER_F64: map, row -> element, local indices
   int np;
+  int64_t ng;         // EPI_SCATTER_F64: length of out_f64 (checked build)
   const CgState *st;  // optional: skip the launch when a solve has stopped
   int *err;           // optional: set to 2 if a tensor-core wait gives up
 };
@@ -114,7 +115,11 @@ __device__ __forceinline__ void gemm_store(const GemmArgs &g, int64_t m, int n, 
     if (n < g.nvalid) g.out_f64[o] = (double)v * g.scale[m];
   } else {
     if (n < g.nvalid) {
-      const int32_t gid = idrow[g.lidx[n]];
+      if (BS_CHECK && !idrow) return;  // element index failed its check
+      const int lx = g.lidx[n];
+      if (!chk(bs_pred_index(lx, g.np), BS_CHK_PREC_ENTRY)) return;
+      int32_t gid = idrow[lx];
+      if (!chk(bs_pred_map_entry(gid, g.ng), BS_CHK_PREC_ENTRY)) gid = -1;
       if (gid >= 0) g.out_f64[gid] = (double)v * g.scale[m];
     }
   }

@@ -241,6 +241,8 @@ int bs_problem_create(const bs_map *map, double h, double lambda, const double *
     }
   }
   const int64_t NL = map->NL, NG = map->NG;
+  tab.ne = tabf.ne = tabff.ne = map->E;
+  tab.ng = tabf.ng = tabff.ng = NG;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess && h_coef) e = cudaMalloc(&p->d_coef, sizeof(double) * (map->E + 1));
   if (e == cudaSuccess && h_coef)

@@ -45,6 +45,7 @@ struct OpTab {
   // Ee[a*h + m] = (Kh_am + Kh_a,Nq-1-m) / 2, Eo[a*h + m] = (Kh_am - Kh_a,Nq-1-m) / 2.
   T Ee[(kMaxNq / 2) * (kMaxNq / 2)];
   T Eo[(kMaxNq / 2) * (kMaxNq / 2)];
+  int64_t ne, ng;  // the problem's E and N_G (index checks of the checked build)
 };
 
 template <int NQ>
@@ -84,8 +85,9 @@ __device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
   const int ij = threadIdx.x - le * S::NQ2;
   const int i = ij % NQ, j = ij / NQ;
   const int64_t slot = slot0 + le;
-  const bool active = le < S::EPB && slot < E;
+  bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  if (active && !chk(bs_pred_index(e, tab->ne), BS_CHK_OP_ENTRY)) active = false;
   T *u = s_u_all + (le < S::EPB ? le : 0) * S::NP;
   T ureg[NQ];
   int32_t gid[FUSED ? NQ : 1];  // fused: the encoded id of each node of the column
@@ -95,12 +97,14 @@ __device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
     for (int k = 0; k < NQ; ++k) {
       T v;
       if (FUSED) {
-        const int32_t id = __ldcs(ids + base + k * S::NQ2);
+        int32_t id = __ldcs(ids + base + k * S::NQ2);
+        if (!chk(bs_pred_fused_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         gid[k] = id;
         const int32_t gg = id >= 0 ? id : -2 - id;
         v = id != -1 ? in[gg] : T(0);
       } else if (GATHER_IN) {
-        const int32_t id = __ldcs(ids + base + k * S::NQ2);
+        int32_t id = __ldcs(ids + base + k * S::NQ2);
+        if (!chk(bs_pred_map_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         v = id >= 0 ? in[id] : T(0);
       } else {
         v = __ldcs(in + base + k * S::NQ2);
@@ -161,13 +165,15 @@ __device__ __forceinline__ void ax_elements(int64_t slot0, int64_t E,
 // column pairs along r and along s get their e/o values computed once into
 // shared memory; then each thread contracts one output pair along r (threads
 // with i < h) or along s (the others), and, from its own column in registers,
-// all outputs along t; a last pass sums the three per node.
-template <int NQ>
+// all outputs along t; a last pass sums the three per node.  BT: the block
+// width the element group is sized for (128 for the element kernels; the
+// batched kernel's 256-thread blocks take twice the elements per call).
+template <int NQ, int BT = 128>
 struct EoShape {
   static constexpr int H = NQ / 2;
   static constexpr int NQ2 = NQ * NQ;
   static constexpr int NP = NQ * NQ2;
-  static constexpr int EPB = NQ2 >= 128 ? 1 : 128 / NQ2;  // elements per block
+  static constexpr int EPB = NQ2 >= BT ? 1 : BT / NQ2;  // elements per block
   static constexpr int THREADS = ((EPB * NQ2 + 31) / 32) * 32;
   static constexpr int SMEM = EPB * 4 * NP + 2 * H * H + NQ;  // values of T
 };
@@ -176,9 +182,9 @@ constexpr bool use_eo() {
   return NQ % 2 == 0 && NQ <= 10;
 }
 
-// As ax_elements (same arguments, FUSED likewise), by a block of
-// EoShape<NQ>::THREADS threads; smem holds EoShape<NQ>::SMEM values.
-template <typename T, int NQ, bool GATHER_IN, bool FUSED>
+// As ax_elements (same arguments, FUSED likewise), by a block of at least
+// EoShape<NQ, BT>::THREADS threads; smem holds EoShape<NQ, BT>::SMEM values.
+template <typename T, int NQ, bool GATHER_IN, bool FUSED, int BT = 128>
 __device__ __forceinline__ void ax_elements_eo(int64_t slot0, int64_t E,
                                                const int32_t *__restrict__ order,
                                                const int32_t *__restrict__ ids,
@@ -186,7 +192,7 @@ __device__ __forceinline__ void ax_elements_eo(int64_t slot0, int64_t E,
                                                const OpTab<T> *__restrict__ tab,
                                                const double *__restrict__ coef, T g, T mlam,
                                                T *smem, T *__restrict__ outG, Acc<T> *acc) {
-  using S = EoShape<NQ>;
+  using S = EoShape<NQ, BT>;
   constexpr int H = S::H, NQ2 = S::NQ2, NP = S::NP, HP = NP / 2;
   T *s_Ee = smem + S::EPB * 4 * NP, *s_Eo = s_Ee + H * H, *s_w = s_Eo + H * H;
   __syncthreads();
@@ -199,8 +205,9 @@ __device__ __forceinline__ void ax_elements_eo(int64_t slot0, int64_t E,
   const int ij = threadIdx.x - le * NQ2;
   const int i = ij % NQ, j = ij / NQ;
   const int64_t slot = slot0 + le;
-  const bool active = le < S::EPB && slot < E;
+  bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  if (active && !chk(bs_pred_index(e, tab->ne), BS_CHK_OP_ENTRY)) active = false;
   T *U = smem + (le < S::EPB ? le : 0) * 4 * NP;  // u, then the r outputs
   T *Er = U + NP, *Es = U + 2 * NP, *AS = U + 3 * NP;
   T ureg[NQ];
@@ -211,11 +218,13 @@ __device__ __forceinline__ void ax_elements_eo(int64_t slot0, int64_t E,
     for (int k = 0; k < NQ; ++k) {
       T v;
       if (FUSED) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_fused_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         gid[k] = id;
         v = id != -1 ? in[id >= 0 ? id : -2 - id] : T(0);
       } else if (GATHER_IN) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_map_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         v = id >= 0 ? in[id] : T(0);
       } else {
         v = __ldcs(in + base + k * NQ2);

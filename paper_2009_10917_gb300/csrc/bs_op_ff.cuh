@@ -43,6 +43,7 @@ struct OpTabFF {
   // the even-odd halves OpTab::Ee, OpTab::Eo as float pairs
   float Eeh[(kMaxNq / 2) * (kMaxNq / 2)], Eel[(kMaxNq / 2) * (kMaxNq / 2)];
   float Eoh[(kMaxNq / 2) * (kMaxNq / 2)], Eol[(kMaxNq / 2) * (kMaxNq / 2)];
+  int64_t ne, ng;  // the problem's E and N_G (index checks of the checked build)
 };
 
 // x = h + l exactly up to 2^-48 |x| (see the header comment); integer and
@@ -142,8 +143,9 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
   const int ij = threadIdx.x - le * NQ2;
   const int i = ij % NQ, j = ij / NQ;
   const int64_t slot = slot0 + le;
-  const bool active = le < S::EPB && slot < E;
+  bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  if (active && !chk(bs_pred_index(e, tab->ne), BS_CHK_OP_ENTRY)) active = false;
   float *uh = s_uh_all + (le < S::EPB ? le : 0) * S::NP;
   float *ul = s_ul_all + (le < S::EPB ? le : 0) * S::NP;
   float rh[NQ], rl[NQ];
@@ -154,11 +156,13 @@ __device__ __forceinline__ void ax_elements_ff(int64_t slot0, int64_t E,
     for (int k = 0; k < NQ; ++k) {
       double v;
       if (FUSED) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_fused_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         gid[k] = id;
         v = id != -1 ? in[id >= 0 ? id : -2 - id] : 0.0;
       } else if (GATHER_IN) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_map_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         v = id >= 0 ? in[id] : 0.0;
       } else {
         v = __ldcs(in + base + k * NQ2);
@@ -228,14 +232,14 @@ __device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
 // The even-odd form of bs_op.cuh (ax_elements_eo) in float-float arithmetic:
 // the same phases, every value a float pair (e/o values by ff_add, the
 // half-length contractions by ff_fma), result W3 (c (h/2) sum + lambda
-// (h/2)^3 u) joined into a double.  smem holds EoShape<NQ>::SMEM_FF floats.
-template <int NQ>
+// (h/2)^3 u) joined into a double.  smem holds EoShapeFF<NQ, BT>::SMEM floats.
+template <int NQ, int BT = 128>
 struct EoShapeFF {
-  static constexpr int SMEM = EoShape<NQ>::EPB * 8 * EoShape<NQ>::NP +
-                              4 * EoShape<NQ>::H * EoShape<NQ>::H + 2 * NQ;
+  using S = EoShape<NQ, BT>;
+  static constexpr int SMEM = S::EPB * 8 * S::NP + 4 * S::H * S::H + 2 * NQ;
 };
 
-template <int NQ, bool GATHER_IN, bool FUSED>
+template <int NQ, bool GATHER_IN, bool FUSED, int BT = 128>
 __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
                                                   const int32_t *__restrict__ order,
                                                   const int32_t *__restrict__ ids,
@@ -246,7 +250,7 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
                                                   double mlam, float *smem,
                                                   double *__restrict__ outG,
                                                   Acc<double> *acc) {
-  using S = EoShape<NQ>;
+  using S = EoShape<NQ, BT>;
   constexpr int H = S::H, NQ2 = S::NQ2, NP = S::NP, HP = NP / 2, HH = H * H;
   float *s_t = smem + S::EPB * 8 * NP;  // Eeh, Eel, Eoh, Eol, wh, wl
   __syncthreads();
@@ -265,8 +269,9 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
   const int ij = threadIdx.x - le * NQ2;
   const int i = ij % NQ, j = ij / NQ;
   const int64_t slot = slot0 + le;
-  const bool active = le < S::EPB && slot < E;
+  bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  if (active && !chk(bs_pred_index(e, tab->ne), BS_CHK_OP_ENTRY)) active = false;
   float *Uh = smem + (le < S::EPB ? le : 0) * 8 * NP, *Ul = Uh + NP;  // u, then r outputs
   float *Erh = Uh + 2 * NP, *Erl = Uh + 3 * NP, *Esh = Uh + 4 * NP, *Esl = Uh + 5 * NP;
   float *ASh = Uh + 6 * NP, *ASl = Uh + 7 * NP;
@@ -278,11 +283,13 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
     for (int k = 0; k < NQ; ++k) {
       double v;
       if (FUSED) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_fused_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         gid[k] = id;
         v = id != -1 ? in[id >= 0 ? id : -2 - id] : 0.0;
       } else if (GATHER_IN) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_map_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         v = id >= 0 ? in[id] : 0.0;
       } else {
         v = __ldcs(in + base + k * NQ2);
@@ -513,8 +520,9 @@ __global__ void __launch_bounds__(GeoShape<NQ>::THREADS)
   const int ij = threadIdx.x - le * NQ2;
   const int i = ij % NQ, j = ij / NQ;
   const int64_t slot = (int64_t)blockIdx.x * S::EPB + le;
-  const bool active = le < S::EPB && slot < E;
+  bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  if (active && !chk(bs_pred_index(e, tab->ne), BS_CHK_OP_ENTRY)) active = false;
   const int off = (le < S::EPB ? le : 0) * NP;
   float *uh = s_uh + off, *ul = s_ul + off;
   float *frh = s_frh + off, *frl = s_frl + off, *fsh = s_fsh + off, *fsl = s_fsl + off;
@@ -525,7 +533,8 @@ __global__ void __launch_bounds__(GeoShape<NQ>::THREADS)
     for (int k = 0; k < NQ; ++k) {
       double v;
       if (GATHER_IN) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_map_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         v = id >= 0 ? in[id] : 0.0;
       } else {
         v = __ldcs(in + base + k * NQ2);
@@ -645,8 +654,8 @@ int apply_A_global(const bs_problem *P, bool ff, const OpTab<T> *tab, const T *p
                       : launch_ax_geo<true>(P->N, m->E, m->NL, m->d_elem_order, m->d_ids, p, ApL,
                                             P->d_tab, P->d_coef, P->d_geo, P->lambda, st, s))
         return rc;
-      return launch_gather_rows<T, DOT, Ep>(m, false, ApL, Ap, DOT ? p : nullptr,
-                                            P->d_partials, P->d_counter, nullptr, 0, ep, st, s);
+      return launch_gather<T, DOT, Ep>(m, ApL, Ap, DOT ? p : nullptr, P->d_partials,
+                                       P->d_counter, ep, st, s);
     } else {
       return fail(BS_ERR_ARG, "FP32 operator not available with geometric factors");
     }
@@ -674,6 +683,9 @@ int apply_A_global(const bs_problem *P, bool ff, const OpTab<T> *tab, const T *p
                                           P->d_coef, g, mlam, st, s);
   }
   if (rc) return rc;
+  if (!fused)
+    return launch_gather<T, DOT, Ep>(m, ApL, Ap, DOT ? p : nullptr, P->d_partials, P->d_counter,
+                                     ep, st, s);
   return launch_gather_rows<T, DOT, Ep>(m, fused, ApL, Ap, DOT ? p : nullptr, P->d_partials,
                                         P->d_counter, opp, opp ? ax_blocks(P->N, m->E) : 0, ep,
                                         st, s);

@@ -51,8 +51,9 @@ __global__ void __launch_bounds__(GeoShape<NQ>::THREADS)
   const int ij = threadIdx.x - le * NQ2;
   const int i = ij % NQ, j = ij / NQ;
   const int64_t slot = (int64_t)blockIdx.x * S::EPB + le;
-  const bool active = le < S::EPB && slot < E;
+  bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
+  if (active && !chk(bs_pred_index(e, tab->ne), BS_CHK_OP_ENTRY)) active = false;
   const int off = (le < S::EPB ? le : 0) * NP;
   double *u = s_u + off, *fr = s_fr + off, *fs = s_fs + off;
   double ureg[NQ], ft[NQ];
@@ -62,7 +63,8 @@ __global__ void __launch_bounds__(GeoShape<NQ>::THREADS)
     for (int k = 0; k < NQ; ++k) {
       double v;
       if (GATHER_IN) {
-        const int32_t id = __ldcs(ids + base + k * NQ2);
+        int32_t id = __ldcs(ids + base + k * NQ2);
+        if (!chk(bs_pred_map_entry(id, tab->ng), BS_CHK_OP_ENTRY)) id = -1;
         v = id >= 0 ? in[id] : 0.0;
       } else {
         v = __ldcs(in + base + k * NQ2);

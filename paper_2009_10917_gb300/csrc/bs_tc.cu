@@ -193,7 +193,10 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(GemmArgs g, int *err) {
     const int quarter = warp & 3, half = warp >> 2;
     const int64_t m = m0 + quarter * 32 + lane;
     const int32_t *idrow = nullptr;
-    if (EPI == EPI_SCATTER_F64 && m < g.M) idrow = g.ids + (int64_t)(g.order ? g.order[m] : m) * g.np;
+    if (EPI == EPI_SCATTER_F64 && m < g.M) {
+      const int64_t em = g.order ? g.order[m] : m;
+      idrow = chk(bs_pred_index(em, g.M), BS_CHK_PREC_ENTRY) ? g.ids + em * g.np : nullptr;
+    }
     for (int c0 = half * 16; c0 < npad; c0 += 32) {
       uint32_t v[16];
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;

@@ -179,3 +179,30 @@ def test_batched_rejects_bad_config_and_flags():
     rc, _ = bs.solve_batched(probs, b, x, flags=bs.BS_CG_REFINED_F32 | bs.BS_CG_FF_OPERATOR,
                              check=False)
     assert rc == bs.BS_ERR_ARG
+
+
+@pytest.mark.parametrize("flags", [0, bs.BS_CG_FF_OPERATOR, bs.BS_CG_REFINED_F32])
+def test_batched_even_odd_and_direct_element_forms(flags):
+    """Odd degrees (even N+1) run the batched element phase in the even-odd
+    form by default and in the direct form under BS_OP_DIRECT: both converge
+    to the oracle's solution, within the iteration-count bound of each other
+    (the two forms differ by rounding only).  With FP32 inner solves the inner
+    count swings by more than a tenth with rounding alone (FP32 CG loses
+    orthogonality within tens of iterations), so there the outer counts are
+    compared (within 1) and both true residuals checked."""
+    cases = make([(3, 3), (5, 2), (7, 2), (1, 4), (4, 3)], 800)
+    prev = bs.operator_mode(bs.BS_OP_DIRECT)
+    try:
+        rc_d, inf_d, x_d = run(cases, 1e-9, flags=flags)
+    finally:
+        bs.operator_mode(prev)
+    rc_e, inf_e, x_e = run(cases, 1e-9, flags=flags)
+    assert rc_d == 0 and rc_e == 0
+    for (m, Z, P, b), a, c, xa, xc in zip(cases, inf_d, inf_e, x_d, x_e):
+        if flags & bs.BS_CG_REFINED_F32:
+            assert abs(a["outer"] - c["outer"]) <= 1
+        else:
+            assert abs(a["iterations"] - c["iterations"]) <= max(3, 0.02 * a["iterations"])
+        for x in (xa, xc):
+            r = b - oracle.apply_A(m.E, m.N, m.h, 1.0, m.ids, m.NG, x)
+            assert np.linalg.norm(r) <= 1.5e-9 * np.linalg.norm(b)

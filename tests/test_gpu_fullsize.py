@@ -194,3 +194,41 @@ def test_forward_element_by_element(split, odd):
     assert np.all(err <= bound), float((err / np.maximum(S, 1e-300)).max())
     # and the entries agree closely almost everywhere (a flip is rare)
     assert np.mean(err <= 1e-5 * S) >= 0.9
+
+
+def test_gradients_element_by_element():
+    """dL/dW2 entry by entry, dL/dW1 entry by entry for all but rare entries.
+    With dy = 2 (y - t) / (B D) and h the hidden activations, dW2_ij =
+    sum_b dy_bi h_bj.  The two sides differ by the bf16 rounding of dy on the
+    GPU (2^-9 relative per term), one-ulp flips of hidden values (2^-7) and
+    the forward output's own bound (2^-7 S_y, carried into dy):
+      |dW2 - dW2_oracle|_ij <= 2^-6 sum_b |dy_bi| |h_bj| + (2 / (B D)) 2^-7 sum_b S_y,bi |h_bj|.
+    dW1 also passes through relu'(W1 x), whose value flips where a hidden
+    pre-activation lies within rounding of 0; outside those entries the same
+    kind of bound holds, so 99% of the entries must meet it and the whole
+    tensor stays within 1e-2 relative."""
+    D, H, B = 216, 256, 256
+    W1 = (synth.uniform(H * D, 42, 0).reshape(H, D) * np.sqrt(3.0 / D)).astype(np.float32)
+    W2 = (synth.uniform(D * H, 42, 1).reshape(D, H) * np.sqrt(3.0 / H)).astype(np.float32)
+    X = synth.uniform(B * D, 43).reshape(B, D).astype(np.float32)
+    T = synth.uniform(B * D, 44).reshape(B, D).astype(np.float32)
+    net = bs.MLP(W1, W2)
+    loss, g1, g2 = net.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    g1, g2 = g1.cpu().numpy().astype(np.float64), g2.cpu().numpy().astype(np.float64)
+    lo, g1o, g2o = oracle.mlp_loss_grad(W1, W2, X, T, prec=oracle.PREC_BF16)
+    Yo, _ = oracle.mlp_forward(W1, W2, X, prec=oracle.PREC_BF16)
+    xb, w1b, w2b = (oracle.bf16_round(a).astype(np.float64) for a in (X, W1, W2))
+    h = np.maximum(xb @ w1b.T, 0.0)
+    scale = 2.0 / (B * D)
+    dy = scale * (Yo - T.astype(np.float64))
+    Sy = h @ np.abs(w2b.T)
+    bound2 = 2.0 ** -6 * (np.abs(dy).T @ h) + scale * 2.0 ** -7 * (Sy.T @ h)
+    err2 = np.abs(g2 - g2o)
+    assert np.all(err2 <= bound2 + 1e-30), float((err2 / (bound2 + 1e-300)).max())
+    mask = (xb @ w1b.T) > 0.0
+    S1 = (mask * (np.abs(dy) @ np.abs(w2b))).T @ np.abs(xb)
+    E1 = (mask * (scale * 2.0 ** -7 * Sy @ np.abs(w2b))).T @ np.abs(xb)
+    bound1 = 2.0 ** -6 * S1 + E1
+    err1 = np.abs(g1 - g1o)
+    assert np.mean(err1 <= bound1 + 1e-30) >= 0.99
+    assert np.linalg.norm(g1 - g1o) <= 1e-2 * np.linalg.norm(g1o)

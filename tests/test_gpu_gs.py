@@ -113,3 +113,22 @@ def test_gather_negative_zero_sums():
     g = Z.gather(torch.from_numpy(ql).cuda()).cpu().numpy()
     assert np.array_equal(bits(g), bits(oracle.gather(m.ids, ql, m.NG)))
     assert np.all(bits(g) == 0)
+
+
+@pytest.mark.parametrize("K,N", [(4, 3), (3, 2), (5, 7)])
+def test_gather_paths_agree(K, N):
+    """The FP64 gather runs the pipelined kernel (16-byte chunks of q_L staged
+    by cp.async) when N_L is even and q_L is 16-byte aligned, and the
+    staged-tile kernel otherwise (odd N_L; a q_L that starts 8 bytes into a
+    buffer); every path is bitwise the oracle's ascending-order sum, with and
+    without masked entries."""
+    m = synth.Mesh(K, N, seed=K * 7 + N)
+    for ids in (m.ids, masked(m, 0.05, 11)):
+        Z = bs.Map(m.E, N, m.NG, ids)
+        ql = synth.uniform(m.NL, 12)
+        want = oracle.gather(ids, ql, m.NG)
+        buf = torch.zeros(m.NL + 1, dtype=torch.float64, device="cuda")
+        buf[1:] = torch.from_numpy(ql).cuda()
+        for qlt in (torch.from_numpy(ql).cuda(), buf[1:]):
+            g = Z.gather(qlt).cpu().numpy()
+            assert np.array_equal(bits(g), bits(want))
