@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "per-op HBM GB/s (% of GB300 peak); time-to-1e-8 CG solve, plain vs batched/learned"
 OPS = ["copy", "axpy", "norm", "dot", "cg_update", "scatter", "gather"]
-KERNEL_OF = {"copy": "k_copy", "axpy": "k_axpy", "norm": "k_dot", "dot": "k_dot",
-             "cg_update": "k_cg_update", "scatter": "k_scatter2", "gather": "k_gather"}
+KERNEL_OF = {"copy": "k_copy", "axpy": "k_axpy", "norm": "k_norm_split", "dot": "k_dot",
+             "cg_update": "k_cg_update", "scatter": "k_scatter2", "gather": "k_gather_async"}
 
 
 def parse():
@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="default run: skip the compact batched section")
     ap.add_argument("--nsolves", type=int, default=256, help="solves in the batched workload")
+    ap.add_argument("--nsolves-small", type=int, default=1024,
+                    help="solves in the batched workload's small-solve mix (0: skip it)")
     ap.add_argument("--cg-mesh", default="7,48", help="N,K of the CG time-to-tolerance mesh")
     ap.add_argument("--no-cg-small", action="store_true", help="skip the N=3, 8^3 CG runs")
     return ap.parse_args()
@@ -626,6 +628,69 @@ def batched_section(args, compact=False):
     return out
 
 
+def batched_small_section(args):
+    """The launch-bound regime of batching: nsolves_small solves on small
+    meshes (N uniform in {2..8}, K uniform in {2..5}, seed 11; 125 to 68921
+    unknowns each), lambda = 1, tol 1e-8, FP64 arithmetic on both sides, so
+    that the batched solver's only advantage is one cooperative launch per
+    iteration for all solves instead of a graph replay per solve.  Times the
+    batched solver (default and tuned configuration) against the same solves
+    one at a time (CUDA graphs), after an untimed warm-up of each."""
+    import time
+
+    import torch
+
+    from paper_2009_10917_gb300 import bs, synth
+    specs = synth.batched_specs(args.nsolves_small, 11, kmin=2, kmax=5)
+    probs, bs_, keep = [], [], []
+    for i, (N, K) in enumerate(specs):
+        m = synth.Mesh(K, N, seed=5000 + i)
+        Z = bs.Map(m.E, N, m.NG, m.ids)
+        keep.append(Z)
+        probs.append(bs.Problem(Z, m.h, 1.0))
+        bs_.append(torch.from_numpy(synth.uniform(m.NG, 5000 + i, stream=3)).cuda())
+    xs = [torch.zeros_like(b) for b in bs_]
+    out = {"nsolves": len(specs), "sum_N_G": int(sum((k * n + 1) ** 3 for n, k in specs)),
+           "max_N_G": int(max((k * n + 1) ** 3 for n, k in specs))}
+
+    def timed(fn):
+        fn(16)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn(1000000)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    t0 = time.perf_counter()
+    cfg, ms = bs.autotune_batched(probs, bs_, flags=0, iters=8)
+    out["autotune_fp64"] = {"config": cfg.as_dict(), "ms_per_iteration": round(ms, 3),
+                            "tuning_seconds": round(time.perf_counter() - t0, 2)}
+    for name, c in (("batched_fp64", None), ("batched_fp64_tuned", cfg)):
+        dt, (rc, infos) = timed(lambda it: bs.solve_batched(
+            probs, bs_, xs, tol=1e-8, maxit=it, flags=bs.BS_CG_GRAPH, check=False, config=c))
+        out[name] = {"seconds": round(dt, 3), "rc": rc,
+                     "max_rel_residual": max(i["rel_residual"] for i in infos),
+                     "iterations_sum": sum(i["iterations"] for i in infos),
+                     "iterations_max": max(i["iterations"] for i in infos)}
+
+    def one_by_one(maxit):
+        worst, its = 0.0, 0
+        for P, b in zip(probs, bs_):
+            _, info = P.cg(b, tol=1e-8, maxit=min(maxit, 100000), flags=bs.BS_CG_GRAPH,
+                           check=False)
+            worst = max(worst, info["rel_residual"])
+            its += info["iterations"]
+        return worst, its
+
+    dt, (worst, its) = timed(one_by_one)
+    out["sequential_fp64"] = {"seconds": round(dt, 3), "max_rel_residual": worst,
+                              "iterations_sum": its}
+    best = min(("batched_fp64", "batched_fp64_tuned"), key=lambda k: out[k]["seconds"])
+    out["speedup_batched_fp64_vs_sequential_fp64"] = round(
+        out["sequential_fp64"]["seconds"] / out[best]["seconds"], 3)
+    return out
+
+
 def learned_section(args, compact=False):
     """The learned-preconditioner configuration: degree N=5 on a 64^3 mesh
     (E = 262144, N_G = 321^3), lambda = 1e-2, per-element coefficient
@@ -1041,9 +1106,11 @@ if __name__ == "__main__":
     elif a.workload == "batched":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        print(json.dumps({"metric": "time-to-1e-8 CG solve, batched vs one at a time",
-                          "unit": "s", "higher_is_better": False,
-                          "batched": batched_section(a)}), flush=True)
+        res = {"metric": "time-to-1e-8 CG solve, batched vs one at a time",
+               "unit": "s", "higher_is_better": False, "batched": batched_section(a)}
+        if a.nsolves_small > 0:
+            res["batched_small"] = batched_small_section(a)
+        print(json.dumps(res), flush=True)
     elif a.workload == "learned":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

@@ -52,7 +52,8 @@ def _deps():
 
 # Sources of the seven BS kernels (BS1-BS7) and the device helpers they
 # include (the C header holds declarations only): BS1-BS5, BS7, BS6.
-STREAM_SOURCES = ("bs_internal.cuh", "bs_stream.cuh", "bs_stream.cu")
+STREAM_SOURCES = ("bs_internal.cuh", "bs_check.cuh", "bs_check_pred.h", "bs_stream.cuh",
+                  "bs_stream.cu")
 SCATTER_SOURCES = STREAM_SOURCES + ("bs_gs.cuh", "bs_gs.cu")
 GATHER_SOURCES = SCATTER_SOURCES + ("bs_gather.cuh",)
 OP_SOURCES = {"copy": STREAM_SOURCES, "axpy": STREAM_SOURCES, "norm": STREAM_SOURCES,
