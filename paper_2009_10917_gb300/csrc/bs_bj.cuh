@@ -123,13 +123,13 @@ __global__ void __launch_bounds__(256)
   constexpr int NN = NI * NI * NI;
   constexpr int EPB = NN >= 256 ? 1 : 256 / NN;
   constexpr int PER = (NN + 255) / 256;
-  __shared__ float s_ah[EPB * NN], s_al[EPB * NN], s_bh[EPB * NN], s_bl[EPB * NN];
-  __shared__ float s_Vh[NI * NI], s_Vl[NI * NI];
+  // float pairs as float2 (hi, lo): one 8-byte shared access per value
+  __shared__ float2 s_a[EPB * NN], s_b[EPB * NN];
+  __shared__ float2 s_V[NI * NI];
   __shared__ float s_ch[EPB], s_cl[EPB];
   if (!init && cg_halted(st)) return;
   for (int t = threadIdx.x; t < NI * NI; t += 256) {
-    s_Vh[t] = tab->Vh[t];
-    s_Vl[t] = tab->Vl[t];
+    s_V[t] = make_float2(tab->Vh[t], tab->Vl[t]);
   }
   // a power of two bringing the residual's RMS near 1, when it lies far from it
   const double rr = init ? st->rr : st->rr_next;
@@ -142,10 +142,11 @@ __global__ void __launch_bounds__(256)
   const FF ml = ff_split(mlam);
   const int Nq = N + 1, Np = Nq * Nq * Nq;
   double acc = 0.0;
-  // the map entries (and qualification flags) of a group of elements: loaded
-  // one group ahead, so that the dependent loads of r and D^-1 are the only
-  // memory latency a group waits for
-  int32_t nid[PER];
+  // Pipelined loads: while a group of elements is transformed, the r and D^-1
+  // values and the coefficients of the next group and the map entries and
+  // qualification flags of the group after it are in flight, so that a group
+  // waits for no memory access of its own.
+  int32_t nid[PER];  // map entries, two groups ahead
   uint8_t nq[PER];
   auto load_ids = [&](int64_t e0) {
 #pragma unroll
@@ -159,33 +160,51 @@ __global__ void __launch_bounds__(256)
       nq[u] = valid ? qual[e] : 0;
     }
   };
-  const int64_t gstep = (int64_t)gridDim.x * EPB;
-  load_ids((int64_t)blockIdx.x * EPB);
-  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < E; e0 += gstep) {
+  int32_t vgid[PER];  // the next group: global node (-1: not transformed), r, D^-1
+  double vr[PER], vd[PER], vc = 1.0;
+  auto load_vals = [&](int64_t e0) {  // from nid / nq, the map entries of group e0
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      vgid[u] = nq[u] && nid[u] >= 0 ? nid[u] : -1;
+      vr[u] = vgid[u] >= 0 ? r[vgid[u]] : 0.0;
+      vd[u] = vgid[u] >= 0 ? dinv[vgid[u]] : 0.0;
+    }
     if (threadIdx.x < EPB) {
       const int64_t e = e0 + threadIdx.x;
-      const FF c = ff_split((coef && e < E ? coef[e] : 1.0) * g);
-      s_ch[threadIdx.x] = c.hi;
-      s_cl[threadIdx.x] = c.lo;
+      vc = coef && e < E ? coef[e] : 1.0;
     }
+  };
+  const int64_t gstep = (int64_t)gridDim.x * EPB, first = (int64_t)blockIdx.x * EPB;
+  load_ids(first);
+  load_vals(first);
+  if (first + gstep < E) load_ids(first + gstep);
+  for (int64_t e0 = first; e0 < E; e0 += gstep) {
     int32_t gid[PER];
     double rv[PER], dv[PER];
     bool on[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      on[u] = nq[u] && nid[u] >= 0;
-      gid[u] = nid[u];
-      rv[u] = on[u] ? r[gid[u]] : 0.0;
-      dv[u] = on[u] ? dinv[gid[u]] : 0.0;
+      gid[u] = vgid[u];
+      on[u] = gid[u] >= 0;
+      rv[u] = vr[u];
+      dv[u] = vd[u];
     }
-    if (e0 + gstep < E) load_ids(e0 + gstep);
+    const double cv = vc;
+    if (e0 + gstep < E) {
+      load_vals(e0 + gstep);
+      if (e0 + 2 * gstep < E) load_ids(e0 + 2 * gstep);
+    }
+    if (threadIdx.x < EPB) {
+      const FF c = ff_split(cv * g);
+      s_ch[threadIdx.x] = c.hi;
+      s_cl[threadIdx.x] = c.lo;
+    }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int f = threadIdx.x + 256 * u;
       const FF x = on[u] ? ff_split(k ? rv[u] * down : rv[u]) : FF{0.f, 0.f};
       if (f < EPB * NN) {
-        s_ah[f] = x.hi;
-        s_al[f] = x.lo;
+        s_a[f] = make_float2(x.hi, x.lo);
       }
     }
     __syncthreads();
@@ -193,8 +212,8 @@ __global__ void __launch_bounds__(256)
     // Buffers alternate a -> b -> a ...; after six passes the result is in a.
 #pragma unroll
     for (int pass = 0; pass < 6; ++pass) {
-      const float *inh = (pass & 1) ? s_bh : s_ah, *inl = (pass & 1) ? s_bl : s_al;
-      float *outh = (pass & 1) ? s_ah : s_bh, *outl = (pass & 1) ? s_al : s_bl;
+      const float2 *in = (pass & 1) ? s_b : s_a;
+      float2 *out = (pass & 1) ? s_a : s_b;
       const int dim = pass % 3;
       const bool fwd = pass < 3;
 #pragma unroll
@@ -209,7 +228,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int m = 0; m < NI; ++m) {
             const int v = fwd ? m * NI + ix : ix * NI + m;
-            ff_fma(s, s_Vh[v], s_Vl[v], inh[base + m * stride], inl[base + m * stride]);
+            const float2 vv = s_V[v], xv = in[base + m * stride];
+            ff_fma(s, vv.x, vv.y, xv.x, xv.y);
           }
           s = ff_norm(s);
           if (pass == 2) {  // divide by d = c_e (h/2)(mu_a + mu_b + mu_c) + lambda (h/2)^3
@@ -223,8 +243,7 @@ __global__ void __launch_bounds__(256)
             ff_fma(o, s.hi, s.lo, x0, x0 * err);
             s = ff_norm(o);
           }
-          outh[f] = s.hi;
-          outl[f] = s.lo;
+          out[f] = make_float2(s.hi, s.lo);
         }
       }
       __syncthreads();
@@ -233,7 +252,8 @@ __global__ void __launch_bounds__(256)
     for (int u = 0; u < PER; ++u) {
       if (!on[u]) continue;
       const int f = threadIdx.x + 256 * u;
-      double zv = ff_widen(s_ah[f]) + ff_widen(s_al[f]);
+      const float2 zf = s_a[f];
+      double zv = ff_widen(zf.x) + ff_widen(zf.y);
       if (k) zv = zv * up;
       z[gid[u]] = zv;
       acc = fma(rv[u], fma(-dv[u], rv[u], zv), acc);

@@ -82,7 +82,7 @@ int register_check_word(int (*read_and_clear)(unsigned int *)) {
   return (int)check_readers().size();
 }
 
-static const char *check_code_name(unsigned int code) {
+[[maybe_unused]] static const char *check_code_name(unsigned int code) {
   switch (code) {
     case BS_CHK_SCATTER_ENTRY: return "scatter: map entry >= N_G";
     case BS_CHK_GATHER_TILE: return "gather: tile bounds outside the CSR";
@@ -141,7 +141,9 @@ int bs_version(void) { return 10000; }
 int bs_check_enabled(void) { return BS_CHECK ? 1 : 0; }
 
 int bs_check_device(void) {
-  if (!BS_CHECK) return BS_OK;
+#if !BS_CHECK
+  return BS_OK;
+#else
   BS_CUDA_TRY(cudaDeviceSynchronize());
   unsigned int first = 0;
   int nfail = 0;
@@ -158,6 +160,7 @@ int bs_check_device(void) {
     return bs::fail(BS_ERR_DEVICE_CHECK, "device check %u (%s) failed in %d unit(s)", first,
                     bs::check_code_name(first), nfail);
   return BS_OK;
+#endif
 }
 
 int bs_workspace_create(bs_workspace **ws) {

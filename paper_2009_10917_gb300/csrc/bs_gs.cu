@@ -84,8 +84,10 @@ static std::vector<int2> make_tiles(const std::vector<int32_t> &rs, int64_t nrow
 // tile holds at most kAgEntries CSR entries, kAgRows rows and kAgChunks
 // distinct 16-byte chunks of q_L; per tile the sorted chunk ids, then a blob
 // of uint16 entry offsets (slot * 2 + the value's half of its chunk) and
-// uint16 row starts relative to the tile's first entry, each padded to 8
-// values.  A row that alone exceeds a tile gets a tile of its own marked -1.
+// uint16 row starts relative to the tile's first entry, then the tile's rows
+// (uint16, relative to its first row) in the order the kernel sums them, each
+// part padded to 8 values.  A row that alone exceeds a tile gets a tile of its
+// own marked -1.
 struct AgTiles {
   std::vector<int4> info;
   std::vector<int32_t> chunks;
@@ -142,6 +144,14 @@ static AgTiles build_async_tiles(const std::vector<int32_t> &rs, const std::vect
       }
       while (T.blob.size() % 8) T.blob.push_back(0);
       for (int64_t q = g; q <= r; ++q) T.blob.push_back((uint16_t)(rs[(size_t)q] - k0));
+      while (T.blob.size() % 8) T.blob.push_back(0);
+      // the summing order: rows by length, longest first (stable)
+      std::vector<int32_t> ord((size_t)(r - g));
+      for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int32_t)q;
+      auto len = [&](int32_t q) { return rs[(size_t)g + q + 1] - rs[(size_t)g + q]; };
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](int32_t a, int32_t b) { return len(a) > len(b); });
+      for (int32_t q : ord) T.blob.push_back((uint16_t)q);
       while (T.blob.size() % 8) T.blob.push_back(0);
     }
     T.info.push_back(in);

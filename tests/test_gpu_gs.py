@@ -88,17 +88,25 @@ def test_bad_map_rejected():
     assert e.value.status == bs.BS_ERR_ARG
 
 
-def test_gather_row_longer_than_a_tile():
-    """A global node with more local copies than one gather tile stages (2048)
-    takes the direct path; the sum order stays ascending."""
-    m = synth.Mesh(3, 4, seed=1)
+@pytest.mark.parametrize("K,rows", [(3, [(0, 2500), (3000, 3100)]),
+                                    (4, [(0, 1500), (2000, 2900), (5000, 5030)])])
+def test_gather_row_longer_than_a_tile(K, rows):
+    """A global node with more local copies than a gather tile holds (2048
+    entries for the staged tiles, 1024 for the pipelined ones) is summed
+    straight from the CSR; the sum order stays ascending.  Rows of 2500 and
+    1500 copies (longer than one or both kinds of tile) and of 900, 100 and 30
+    (long but fitting)."""
+    m = synth.Mesh(K, 4, seed=1)
     ids = m.ids.copy()
-    ids[:2500] = 0           # one row of 2500 entries
-    ids[3000:3100] = 7       # and a long-but-fitting one
+    for g, (a, b) in enumerate(rows):
+        ids[a:b] = 7 * g
     Z = bs.Map(m.E, m.N, m.NG, ids)
     ql = synth.uniform(m.NL, 4)
+    want = oracle.gather(ids, ql, m.NG)
     g = Z.gather(torch.from_numpy(ql).cuda()).cpu().numpy()
-    assert np.array_equal(bits(g), bits(oracle.gather(ids, ql, m.NG)))
+    assert np.array_equal(bits(g), bits(want))
+    gf = Z.gather(torch.from_numpy(ql.astype(np.float32)).cuda()).cpu().numpy()
+    assert np.array_equal(bits(gf), bits(oracle.gather_f32(ids, ql.astype(np.float32), m.NG)))
     rs, ci = Z.export()
     ors, oci = oracle.csr(ids, m.NG)
     assert np.array_equal(rs, ors) and np.array_equal(ci, oci)
