@@ -87,7 +87,9 @@ static std::vector<int2> make_tiles(const std::vector<int32_t> &rs, int64_t nrow
 // uint16 row starts relative to the tile's first entry, then the tile's rows
 // (uint16, relative to its first row) in the order the kernel sums them, each
 // part padded to 8 values.  A row that alone exceeds a tile gets a tile of its
-// own marked -1.
+// own marked -1.  With N_L odd the 16-byte chunk of the last local node would
+// run past q_L, so the row holding that node (one row at most) gets a tile of
+// its own marked -1 as well and no chunk covers it.
 struct AgTiles {
   std::vector<int4> info;
   std::vector<int32_t> chunks;
@@ -100,6 +102,12 @@ static AgTiles build_async_tiles(const std::vector<int32_t> &rs, const std::vect
   std::vector<int32_t> mark((size_t)((NL + 1) / 2), -1);
   std::vector<int32_t> ch;
   int32_t tile = 0;
+  // N_L odd: the row holding local node N_L - 1, summed straight from the CSR
+  int64_t direct_row = -1;
+  if (NL % 2 == 1)
+    for (int64_t g = 0; g < NG && direct_row < 0; ++g)
+      if (rs[(size_t)g] < rs[(size_t)g + 1] && col[(size_t)rs[(size_t)g + 1] - 1] == NL - 1)
+        direct_row = g;
   auto row_chunks_new = [&](int64_t r) {  // chunks of row r not yet in the tile
     int fresh = 0;
     for (int32_t k = rs[(size_t)r]; k < rs[(size_t)r + 1]; ++k) {
@@ -114,7 +122,8 @@ static AgTiles build_async_tiles(const std::vector<int32_t> &rs, const std::vect
   for (int64_t g = 0; g < NG;) {
     int64_t r = g;
     ch.clear();
-    while (r < NG && r - g < kAgRows && rs[(size_t)r + 1] - rs[(size_t)g] <= kAgEntries &&
+    while (r < NG && r != direct_row && r - g < kAgRows &&
+           rs[(size_t)r + 1] - rs[(size_t)g] <= kAgEntries &&
            (int)ch.size() + row_chunks_new(r) <= kAgChunks) {
       for (int32_t k = rs[(size_t)r]; k < rs[(size_t)r + 1]; ++k) {
         const int32_t c = col[(size_t)k] >> 1;
@@ -129,7 +138,7 @@ static AgTiles build_async_tiles(const std::vector<int32_t> &rs, const std::vect
     in.x = (int)g;
     in.y = (int)T.chunks.size();
     in.z = (int)(T.blob.size() / 8);
-    if (r == g) {  // one row too long for a tile
+    if (r == g) {  // one row too long for a tile, or the row of the odd last node
       in.w = -1;
       r = g + 1;
     } else {
@@ -274,7 +283,7 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
   if (e == cudaSuccess) e = upload(&m->d_sh_starts, sh_starts);
   if (e == cudaSuccess) e = upload(&m->d_sh_cols, sh_cols, 4);
   if (e == cudaSuccess) e = upload(&m->d_sh_tiles, sh_tiles);
-  if (e == cudaSuccess && NL % 2 == 0 && NG > 0) {  // the pipelined FP64 gather's tiles
+  if (e == cudaSuccess && NG > 0) {  // the pipelined FP64 gather's tiles
     AgTiles T = build_async_tiles(rs, col, NL, NG);
     m->ag_ntiles = (int64_t)T.info.size() - 1;
     e = upload(&m->d_ag_info, T.info);

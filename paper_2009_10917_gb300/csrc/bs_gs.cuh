@@ -35,8 +35,10 @@ struct bs_map {
   int32_t *d_sh_cols;     // [nnz_sh] the rows' CSR entries, ascending local index
   int2 *d_sh_tiles;       // [nsh_tiles + 1]
   // The pipelined FP64 gather (bs_gather.cuh, k_gather_async): per tile the
-  // distinct 16-byte chunks of q_L it reads and a blob of uint16 entry offsets
-  // and row starts; NULL when N_L is odd (a chunk would leave q_L).
+  // distinct 16-byte chunks of q_L it reads and a blob of uint16 entry offsets,
+  // row starts and summing order; NULL when N_G is 0.  With N_L odd the row
+  // holding the last local node is summed from the CSR (its chunk would leave
+  // q_L).
   int64_t ag_ntiles;
   int4 *d_ag_info;        // [ag_ntiles + 1] first row, first chunk, first blob word,
                           // (entries << 16 | rows), or -1: rows summed straight from the CSR

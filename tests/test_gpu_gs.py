@@ -123,15 +123,18 @@ def test_gather_negative_zero_sums():
     assert np.all(bits(g) == 0)
 
 
-@pytest.mark.parametrize("K,N", [(4, 3), (3, 2), (5, 7)])
+@pytest.mark.parametrize("K,N", [(4, 3), (3, 2), (5, 7), (5, 4)])
 def test_gather_paths_agree(K, N):
     """The FP64 gather runs the pipelined kernel (16-byte chunks of q_L staged
-    by cp.async) when N_L is even and q_L is 16-byte aligned, and the
-    staged-tile kernel otherwise (odd N_L; a q_L that starts 8 bytes into a
-    buffer); every path is bitwise the oracle's ascending-order sum, with and
-    without masked entries."""
+    by cp.async) when q_L is 16-byte aligned -- with N_L odd, the row holding
+    the last local node summed from the CSR -- and the staged-tile kernel
+    otherwise (a q_L that starts 8 bytes into a buffer); every path is bitwise
+    the oracle's ascending-order sum, with and without masked entries (which
+    may mask the last local node)."""
     m = synth.Mesh(K, N, seed=K * 7 + N)
-    for ids in (m.ids, masked(m, 0.05, 11)):
+    last_masked = m.ids.copy()
+    last_masked[-1] = -1
+    for ids in (m.ids, masked(m, 0.05, 11), last_masked):
         Z = bs.Map(m.E, N, m.NG, ids)
         ql = synth.uniform(m.NL, 12)
         want = oracle.gather(ids, ql, m.NG)
