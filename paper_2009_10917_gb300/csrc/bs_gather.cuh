@@ -24,7 +24,10 @@
 // and warps waiting on the dependent colIds -> q_L loads).  Loading q_L
 // through the read-only data path (__ldg) instead of as streaming loads gave
 // 6%, probably because an element row read by two neighbouring tiles of the
-// same wave then stays in L1.
+// same wave then stays in L1.  This staged form serves the FP32 gather, a q_L
+// not 16-byte aligned, the fused operator's shared rows and the batched
+// solver; the FP64 gather runs the pipelined form further down (82% of the
+// peak in the same setting).
 #pragma once
 
 #include "bs_gs.cuh"
