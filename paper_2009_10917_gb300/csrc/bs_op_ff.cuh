@@ -252,19 +252,16 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
                                                   Acc<double> *acc) {
   using S = EoShape<NQ, BT>;
   constexpr int H = S::H, NQ2 = S::NQ2, NP = S::NP, HP = NP / 2, HH = H * H;
-  float *s_t = smem + S::EPB * 8 * NP;  // Eeh, Eel, Eoh, Eol, wh, wl
+  // float pairs kept as float2 (hi, lo): one 8-byte shared access per value
+  // (smem is 8-byte aligned)
+  float2 *sm2 = reinterpret_cast<float2 *>(smem);
+  float2 *s_Ee = sm2 + S::EPB * 4 * NP, *s_Eo = s_Ee + HH, *s_w = s_Eo + HH;
   __syncthreads();
   for (int t = threadIdx.x; t < HH; t += blockDim.x) {
-    s_t[t] = tab->Eeh[t];
-    s_t[HH + t] = tab->Eel[t];
-    s_t[2 * HH + t] = tab->Eoh[t];
-    s_t[3 * HH + t] = tab->Eol[t];
+    s_Ee[t] = make_float2(tab->Eeh[t], tab->Eel[t]);
+    s_Eo[t] = make_float2(tab->Eoh[t], tab->Eol[t]);
   }
-  for (int t = threadIdx.x; t < NQ; t += blockDim.x) {
-    s_t[4 * HH + t] = tab->wh[t];
-    s_t[4 * HH + NQ + t] = tab->wl[t];
-  }
-  const float *s_w = s_t + 4 * HH;
+  for (int t = threadIdx.x; t < NQ; t += blockDim.x) s_w[t] = make_float2(tab->wh[t], tab->wl[t]);
   const int le = threadIdx.x / NQ2;
   const int ij = threadIdx.x - le * NQ2;
   const int i = ij % NQ, j = ij / NQ;
@@ -272,9 +269,8 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
   bool active = le < S::EPB && slot < E;
   const int64_t e = active && order ? (int64_t)order[slot] : slot;
   if (active && !chk(bs_pred_index(e, tab->ne), BS_CHK_OP_ENTRY)) active = false;
-  float *Uh = smem + (le < S::EPB ? le : 0) * 8 * NP, *Ul = Uh + NP;  // u, then r outputs
-  float *Erh = Uh + 2 * NP, *Erl = Uh + 3 * NP, *Esh = Uh + 4 * NP, *Esl = Uh + 5 * NP;
-  float *ASh = Uh + 6 * NP, *ASl = Uh + 7 * NP;
+  float2 *U = sm2 + (le < S::EPB ? le : 0) * 4 * NP;  // u, then the r outputs
+  float2 *Er = U + NP, *Es = U + 2 * NP, *AS = U + 3 * NP;
   float rh[NQ], rl[NQ];
   int32_t gid[FUSED ? NQ : 1];
   if (active) {
@@ -297,53 +293,48 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
       const FF f = ff_split(v);
       rh[k] = f.hi;
       rl[k] = f.lo;
-      Uh[ij + k * NQ2] = f.hi;
-      Ul[ij + k * NQ2] = f.lo;
+      U[ij + k * NQ2] = make_float2(f.hi, f.lo);
     }
   }
   __syncthreads();
   const bool rtask = i < H;
   const int a = rtask ? i : i - H;
   if (active) {
-    float *dh = rtask ? Erh : Esh, *dl = rtask ? Erl : Esl;
+    float2 *dst = rtask ? Er : Es;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
       const int l0 = rtask ? a + NQ * j + NQ2 * k : j + NQ * a + NQ2 * k;
       const int l1 = rtask ? (NQ - 1 - a) + NQ * j + NQ2 * k : j + NQ * (NQ - 1 - a) + NQ2 * k;
-      const FF u0{Uh[l0], Ul[l0]}, u1{Uh[l1], Ul[l1]};
+      const float2 x0 = U[l0], x1 = U[l1];
+      const FF u0{x0.x, x0.y}, u1{x1.x, x1.y};
       const FF ev = ff_add(u0, u1), ov = ff_add(u0, ff_neg(u1));
       const int d = a + H * (j + NQ * k);
-      dh[d] = ev.hi;
-      dl[d] = ev.lo;
-      dh[HP + d] = ov.hi;
-      dl[HP + d] = ov.lo;
+      dst[d] = make_float2(ev.hi, ev.lo);
+      dst[HP + d] = make_float2(ov.hi, ov.lo);
     }
   }
   __syncthreads();
   if (active) {
-    const float *sh = rtask ? Erh : Esh, *sl = rtask ? Erl : Esl;
+    const float2 *src = rtask ? Er : Es;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
       FF se{0.f, 0.f}, so{0.f, 0.f};
 #pragma unroll
       for (int m = 0; m < H; ++m) {
         const int d = m + H * (j + NQ * k);
-        ff_fma(se, s_t[a * H + m], s_t[HH + a * H + m], sh[d], sl[d]);
-        ff_fma(so, s_t[2 * HH + a * H + m], s_t[3 * HH + a * H + m], sh[HP + d], sl[HP + d]);
+        const float2 ce = s_Ee[a * H + m], co = s_Eo[a * H + m], xe = src[d], xo = src[HP + d];
+        ff_fma(se, ce.x, ce.y, xe.x, xe.y);
+        ff_fma(so, co.x, co.y, xo.x, xo.y);
       }
       const FF p = ff_add(se, so), q = ff_add(se, ff_neg(so));
       if (rtask) {
         const int l0 = a + NQ * j + NQ2 * k, l1 = (NQ - 1 - a) + NQ * j + NQ2 * k;
-        Uh[l0] = p.hi;
-        Ul[l0] = p.lo;
-        Uh[l1] = q.hi;
-        Ul[l1] = q.lo;
+        U[l0] = make_float2(p.hi, p.lo);
+        U[l1] = make_float2(q.hi, q.lo);
       } else {
         const int l0 = j + NQ * a + NQ2 * k, l1 = j + NQ * (NQ - 1 - a) + NQ2 * k;
-        ASh[l0] = p.hi;
-        ASl[l0] = p.lo;
-        ASh[l1] = q.hi;
-        ASl[l1] = q.lo;
+        AS[l0] = make_float2(p.hi, p.lo);
+        AS[l1] = make_float2(q.hi, q.lo);
       }
     }
   }
@@ -361,8 +352,9 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
       FF se{0.f, 0.f}, so{0.f, 0.f};
 #pragma unroll
       for (int m = 0; m < H; ++m) {
-        ff_fma(se, s_t[k * H + m], s_t[HH + k * H + m], ev[m].hi, ev[m].lo);
-        ff_fma(so, s_t[2 * HH + k * H + m], s_t[3 * HH + k * H + m], ov[m].hi, ov[m].lo);
+        const float2 ce = s_Ee[k * H + m], co = s_Eo[k * H + m];
+        ff_fma(se, ce.x, ce.y, ev[m].hi, ev[m].lo);
+        ff_fma(so, co.x, co.y, ov[m].hi, ov[m].lo);
       }
       at[k] = ff_add(se, so);
       at[NQ - 1 - k] = ff_add(se, ff_neg(so));
@@ -373,16 +365,17 @@ __device__ __forceinline__ void ax_elements_ff_eo(int64_t slot0, int64_t E,
   const FF cg = ff_split((coef ? coef[e] : 1.0) * g);
   const FF ml = ff_split(mlam);
   FF wij{0.f, 0.f};
-  ff_fma(wij, s_w[i], s_w[NQ + i], s_w[j], s_w[NQ + j]);
+  ff_fma(wij, s_w[i].x, s_w[i].y, s_w[j].x, s_w[j].y);
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
     const int l = ij + NQ2 * k;
-    const FF sum = ff_add(ff_add(FF{Uh[l], Ul[l]}, FF{ASh[l], ASl[l]}), at[k]);
+    const float2 uu = U[l], aa = AS[l];
+    const FF sum = ff_add(ff_add(FF{uu.x, uu.y}, FF{aa.x, aa.y}), at[k]);
     FF o{0.f, 0.f};
     ff_fma(o, cg.hi, cg.lo, sum.hi, sum.lo);
     ff_fma(o, ml.hi, ml.lo, rh[k], rl[k]);
     FF w3{0.f, 0.f};
-    ff_fma(w3, wij.hi, wij.lo, s_w[k], s_w[NQ + k]);
+    ff_fma(w3, wij.hi, wij.lo, s_w[k].x, s_w[k].y);
     FF r{0.f, 0.f};
     ff_fma(r, w3.hi, w3.lo, o.hi, o.lo);
     const double res = ff_widen(r.hi) + ff_widen(r.lo);
@@ -410,7 +403,7 @@ __global__ void __launch_bounds__(EoShape<NQ>::THREADS)
                      const CgState *st, double *__restrict__ outG,
                      double *__restrict__ partials) {
   using S = EoShape<NQ>;
-  __shared__ float smem[EoShapeFF<NQ>::SMEM];
+  __shared__ __align__(16) float smem[EoShapeFF<NQ>::SMEM];
   if (cg_halted(st)) return;
   Acc<double> acc;
   ax_elements_ff_eo<NQ, GATHER_IN, FUSED>((int64_t)blockIdx.x * S::EPB, E, order, ids, in, out,
