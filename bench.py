@@ -303,6 +303,7 @@ def run_ours(args):
         # operations starts as soon as its inputs have arrived
         cstream = torch.cuda.Stream()
         groups = (("x",), ("p", "Ap", "xc", "r"), ("qG",))
+        assert sorted(k_ for g_ in groups for k_ in g_) == sorted(pinned), "e2e copies every input"
         ready = [torch.cuda.Event() for _ in groups]
 
         def e2e_step():
