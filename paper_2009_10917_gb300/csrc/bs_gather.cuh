@@ -24,10 +24,10 @@
 // and warps waiting on the dependent colIds -> q_L loads).  Loading q_L
 // through the read-only data path (__ldg) instead of as streaming loads gave
 // 6%, probably because an element row read by two neighbouring tiles of the
-// same wave then stays in L1.  This staged form serves the FP32 gather, a q_L
-// not 16-byte aligned, the fused operator's shared rows and the batched
-// solver; the FP64 gather runs the pipelined form further down (82% of the
-// peak in the same setting).
+// same wave then stays in L1.  This staged form serves a q_L not aligned to
+// two values, the fused operator's shared rows and the batched solver; the
+// FP64 and FP32 gathers run the pipelined form further down (82% of the peak
+// in the same setting, FP64).
 #pragma once
 
 #include "bs_gs.cuh"
@@ -167,13 +167,13 @@ __global__ void __launch_bounds__(kGatherBlock)
   }
 }
 
-// ------------------------------------------------------------ pipelined FP64 gather
+// ------------------------------------------------------------ pipelined gather (FP64, FP32)
 //
 // The staged-tile gather above waits, tile after tile, on two dependent
 // loads (colIds, then q_L).  This form hides them: the map is re-encoded once
-// per tile as the distinct 16-byte chunks of q_L the tile reads (two values
-// each) and a blob of uint16 entry offsets into those chunks plus uint16 row
-// starts.  A block copies tile t + 1's chunks and blob into shared memory with
+// per tile as the distinct chunks of q_L the tile reads (two values each:
+// 16 bytes in FP64, 8 in FP32, one encoding for both) and a blob of uint16
+// entry offsets into those chunks plus uint16 row starts.  A block copies tile t + 1's chunks and blob into shared memory with
 // cp.async while it sums tile t (two stages), and loads tile t + 2's chunk
 // ids into registers meanwhile, so every global load it waits for was issued
 // a tile earlier.  Sums run over the same entries in the same order as the
@@ -186,17 +186,31 @@ __global__ void __launch_bounds__(kGatherBlock)
 // Tiles of 1024 entries for 256-thread blocks (27 KB of shared memory, eight
 // blocks per SM) ran 1% faster than 2048 for 512 threads; three stages, or
 // 128-thread blocks, were slower.
-constexpr int kAgChunks = 512;    // 16-byte chunks of q_L per tile
+constexpr int kAgChunks = 512;    // chunks of two q_L values per tile
 constexpr int kAgEntries = 1024;  // CSR entries per tile
 constexpr int kAgRows = 768;      // rows per tile
 constexpr int kAgBlob16 =
     ((kAgEntries + 7) / 8 * 8 + (kAgRows + 1 + 7) / 8 * 8 + (kAgRows + 7) / 8 * 8) * 2 / 16;
 constexpr int kAgBlock = 256;
-constexpr int kAgStage = kAgChunks * 16 + kAgBlob16 * 16;
-constexpr int kAgSmem = 2 * kAgStage;
+// One stage: the tile's chunks (two values of T each), then its blob.  The
+// FP32 gather uses the same encoding with 8-byte chunks.
+template <typename T>
+constexpr int ag_stage() {
+  return kAgChunks * 2 * (int)sizeof(T) + kAgBlob16 * 16;
+}
+template <typename T>
+constexpr int ag_smem() {
+  return 2 * ag_stage<T>();
+}
 
 __device__ __forceinline__ void ag_cp16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void ag_cp8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
                    (unsigned)__cvta_generic_to_shared(dst)),
                "l"(src)
                : "memory");
@@ -209,14 +223,15 @@ __device__ __forceinline__ void ag_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <bool DOT, class Ep>
+template <typename T, bool DOT, class Ep>
 __global__ void __launch_bounds__(kAgBlock)
     k_gather_async(int64_t ntiles, const int4 *__restrict__ info,
                    const int32_t *__restrict__ chunks, const uint4 *__restrict__ blob,
                    const int32_t *__restrict__ row_starts, const int32_t *__restrict__ col_ids,
-                   const double *__restrict__ qL, double *__restrict__ qG,
-                   const double *__restrict__ w, double *partials, unsigned int *counter, Ep ep,
-                   const CgState *st, GBounds gb) {
+                   const T *__restrict__ qL, T *__restrict__ qG, const T *__restrict__ w,
+                   double *partials, unsigned int *counter, Ep ep, const CgState *st,
+                   GBounds gb) {
+  constexpr int kStage = ag_stage<T>(), kChunkBytes = 2 * (int)sizeof(T);
   extern __shared__ __align__(16) unsigned char ag_sm[];
   constexpr int CPT = (kAgChunks + kAgBlock - 1) / kAgBlock;  // chunk ids per thread
   if (cg_halted(st)) return;
@@ -248,20 +263,26 @@ __global__ void __launch_bounds__(kAgBlock)
     if (tt < ntiles) {
       const int4 a = info[tt];
       if (a.w >= 0) {
-        unsigned char *base = ag_sm + stage * kAgStage;
+        unsigned char *base = ag_sm + stage * kStage;
 #pragma unroll
-        for (int u = 0; u < CPT; ++u)
-          if (ids[u] >= 0) ag_cp16(base + (threadIdx.x + u * kAgBlock) * 16, qL + 2ll * ids[u]);
+        for (int u = 0; u < CPT; ++u) {
+          if (ids[u] < 0) continue;
+          unsigned char *dst = base + (threadIdx.x + u * kAgBlock) * kChunkBytes;
+          if constexpr (sizeof(T) == 8)
+            ag_cp16(dst, qL + 2ll * ids[u]);
+          else
+            ag_cp8(dst, qL + 2ll * ids[u]);
+        }
         const int b0 = a.z, b1 = info[tt + 1].z;
         if (chk(b0 >= 0 && b0 <= b1 && b1 - b0 <= kAgBlob16 && b1 <= ag_end.z,
                 BS_CHK_GATHER_TILE))
           for (int i = threadIdx.x; i < b1 - b0; i += kAgBlock)
-            ag_cp16(base + kAgChunks * 16 + i * 16, blob + b0 + i);
+            ag_cp16(base + kAgChunks * kChunkBytes + i * 16, blob + b0 + i);
       }
     }
     ag_commit();
   };
-  Acc<double> acc;
+  Acc<T> acc;
   load_ids(t, idsA);
   load_ids(t + G, idsB);
   issue(t, idsA, 0);
@@ -274,9 +295,10 @@ __global__ void __launch_bounds__(kAgBlock)
     const int4 a = info[t];
     const int r0 = a.x;
     if (a.w >= 0) {
-      const unsigned char *base = ag_sm + stage * kAgStage;
-      const double *qv = reinterpret_cast<const double *>(base);
-      const unsigned short *off = reinterpret_cast<const unsigned short *>(base + kAgChunks * 16);
+      const unsigned char *base = ag_sm + stage * kStage;
+      const T *qv = reinterpret_cast<const T *>(base);
+      const unsigned short *off =
+          reinterpret_cast<const unsigned short *>(base + kAgChunks * kChunkBytes);
       int ne = a.w >> 16, rows = a.w & 0xffff;
       const int nst = 2 * (info[t + 1].y - a.y);  // staged values
       if (!chk(ne <= kAgEntries && rows <= kAgRows && r0 >= 0 && r0 + rows <= gb.ng &&
@@ -290,7 +312,7 @@ __global__ void __launch_bounds__(kAgBlock)
         if (!chk(bs_pred_index(r, rows), BS_CHK_GATHER_STAGED)) continue;
         int b0 = rstart[r], b1 = rstart[r + 1];
         if (!chk(bs_pred_row(b0, b1, ne), BS_CHK_GATHER_STAGED)) b0 = b1 = 0;
-        double s = 0.0;
+        T s = T(0);
         if (b0 < b1) {
           const int o = off[b0];
           if (chk(bs_pred_staged(o, nst), BS_CHK_GATHER_STAGED)) s = plus_zero(qv[o]);
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(kAgBlock)
       for (int r = r0 + threadIdx.x; r < r1; r += kAgBlock) {
         int32_t b0 = row_starts[r], b1 = row_starts[r + 1];
         if (!chk(bs_pred_row(b0, b1, gb.nnz), BS_CHK_GATHER_ROW)) b0 = b1 = 0;
-        double s = 0.0;
+        T s = T(0);
         if (b0 < b1) {
           const int32_t c = col_ids[b0];
           if (chk(bs_pred_index(c, gb.nl), BS_CHK_GATHER_COL)) s = plus_zero(qL[c]);
@@ -334,19 +356,19 @@ __global__ void __launch_bounds__(kAgBlock)
   }
 }
 
-template <bool DOT, class Ep>
-int launch_gather_async(const bs_map *m, const double *qL, double *qG, const double *w,
-                        double *partials, unsigned int *counter, Ep ep, const CgState *st,
-                        cudaStream_t s) {
-  auto kern = k_gather_async<DOT, Ep>;
-  const int bps = occupancy_blocks_smem((const void *)kern, kAgBlock, kAgSmem);
-  if (bps < 1) return fail(BS_ERR_CUDA, "pipelined gather: %d B of shared memory refused", kAgSmem);
+template <typename T, bool DOT, class Ep>
+int launch_gather_async(const bs_map *m, const T *qL, T *qG, const T *w, double *partials,
+                        unsigned int *counter, Ep ep, const CgState *st, cudaStream_t s) {
+  auto kern = k_gather_async<T, DOT, Ep>;
+  constexpr int smem = ag_smem<T>();
+  const int bps = occupancy_blocks_smem((const void *)kern, kAgBlock, smem);
+  if (bps < 1) return fail(BS_ERR_CUDA, "pipelined gather: %d B of shared memory refused", smem);
   int grid = stream_grid(m->ag_ntiles, 1, 1, bps);
   if (grid < 1) return fail(BS_ERR_CUDA, "no device");
   if (DOT && grid > kMaxPartials) grid = kMaxPartials;
-  kern<<<grid, kAgBlock, kAgSmem, s>>>(m->ag_ntiles, m->d_ag_info, m->d_ag_chunks, m->d_ag_blob,
-                                       m->d_row_starts, m->d_col_ids, qL, qG, w, partials,
-                                       counter, ep, st, GBounds{m->NG, m->nnz, m->NL, m->NG});
+  kern<<<grid, kAgBlock, smem, s>>>(m->ag_ntiles, m->d_ag_info, m->d_ag_chunks, m->d_ag_blob,
+                                    m->d_row_starts, m->d_col_ids, qL, qG, w, partials, counter,
+                                    ep, st, GBounds{m->NG, m->nnz, m->NL, m->NG});
   BS_LAUNCH_CHECK();
   return BS_OK;
 }
@@ -380,10 +402,9 @@ int launch_gather_rows(const bs_map *m, bool shared, const T *qL, T *qG, const T
 template <typename T, bool DOT, class Ep>
 int launch_gather(const bs_map *m, const T *qL, T *qG, const T *w, double *partials,
                   unsigned int *counter, Ep ep, const CgState *st, cudaStream_t s) {
-  if constexpr (sizeof(T) == 8) {
-    if (m->d_ag_info && ((uintptr_t)qL % 16) == 0)
-      return launch_gather_async<DOT, Ep>(m, qL, qG, w, partials, counter, ep, st, s);
-  }
+  // the pipelined form copies two values per chunk: q_L aligned to 2 sizeof(T)
+  if (m->d_ag_info && ((uintptr_t)qL % (2 * sizeof(T))) == 0)
+    return launch_gather_async<T, DOT, Ep>(m, qL, qG, w, partials, counter, ep, st, s);
   return launch_gather_rows<T, DOT, Ep>(m, false, qL, qG, w, partials, counter, nullptr, 0, ep,
                                         st, s);
 }

@@ -125,12 +125,13 @@ def test_gather_negative_zero_sums():
 
 @pytest.mark.parametrize("K,N", [(4, 3), (3, 2), (5, 7), (5, 4)])
 def test_gather_paths_agree(K, N):
-    """The FP64 gather runs the pipelined kernel (16-byte chunks of q_L staged
-    by cp.async) when q_L is 16-byte aligned -- with N_L odd, the row holding
-    the last local node summed from the CSR -- and the staged-tile kernel
-    otherwise (a q_L that starts 8 bytes into a buffer); every path is bitwise
-    the oracle's ascending-order sum, with and without masked entries (which
-    may mask the last local node)."""
+    """The gather runs the pipelined kernel (chunks of two q_L values staged by
+    cp.async: 16 bytes in FP64, 8 in FP32) when q_L is aligned to a chunk --
+    with N_L odd, the row holding the last local node summed from the CSR --
+    and the staged-tile kernel otherwise (a q_L that starts one value into a
+    buffer); every path, in both precisions, is bitwise the oracle's
+    ascending-order sum, with and without masked entries (which may mask the
+    last local node)."""
     m = synth.Mesh(K, N, seed=K * 7 + N)
     last_masked = m.ids.copy()
     last_masked[-1] = -1
@@ -143,3 +144,10 @@ def test_gather_paths_agree(K, N):
         for qlt in (torch.from_numpy(ql).cuda(), buf[1:]):
             g = Z.gather(qlt).cpu().numpy()
             assert np.array_equal(bits(g), bits(want))
+        qf = ql.astype(np.float32)
+        want_f = oracle.gather_f32(ids, qf, m.NG)
+        buf_f = torch.zeros(m.NL + 1, dtype=torch.float32, device="cuda")
+        buf_f[1:] = torch.from_numpy(qf).cuda()
+        for qlt in (torch.from_numpy(qf).cuda(), buf_f[1:]):
+            g = Z.gather(qlt).cpu().numpy()
+            assert np.array_equal(bits(g), bits(want_f))
