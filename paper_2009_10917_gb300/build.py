@@ -55,7 +55,7 @@ def _deps():
 STREAM_SOURCES = ("bs_internal.cuh", "bs_check.cuh", "bs_check_pred.h", "bs_stream.cuh",
                   "bs_stream.cu")
 SCATTER_SOURCES = STREAM_SOURCES + ("bs_gs.cuh", "bs_gs.cu")
-GATHER_SOURCES = SCATTER_SOURCES + ("bs_gather.cuh",)
+GATHER_SOURCES = SCATTER_SOURCES + ("bs_gather.cuh", "bs_tiles.h")
 OP_SOURCES = {"copy": STREAM_SOURCES, "axpy": STREAM_SOURCES, "norm": STREAM_SOURCES,
               "dot": STREAM_SOURCES, "cg_update": STREAM_SOURCES, "scatter": SCATTER_SOURCES,
               "gather": GATHER_SOURCES}

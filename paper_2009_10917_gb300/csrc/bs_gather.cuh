@@ -31,6 +31,7 @@
 #pragma once
 
 #include "bs_gs.cuh"
+#include "bs_tiles.h"
 
 namespace bs {
 
@@ -186,11 +187,7 @@ __global__ void __launch_bounds__(kGatherBlock)
 // Tiles of 1024 entries for 256-thread blocks (27 KB of shared memory, eight
 // blocks per SM) ran 1% faster than 2048 for 512 threads; three stages, or
 // 128-thread blocks, were slower.
-constexpr int kAgChunks = 512;    // chunks of two q_L values per tile
-constexpr int kAgEntries = 1024;  // CSR entries per tile
-constexpr int kAgRows = 768;      // rows per tile
-constexpr int kAgBlob16 =
-    ((kAgEntries + 7) / 8 * 8 + (kAgRows + 1 + 7) / 8 * 8 + (kAgRows + 7) / 8 * 8) * 2 / 16;
+// tile sizes kAgChunks, kAgEntries, kAgRows and kAgBlob16: bs_tiles.h
 constexpr int kAgBlock = 256;
 // One stage: the tile's chunks (two values of T each), then its blob.  The
 // FP32 gather uses the same encoding with 8-byte chunks.

@@ -80,102 +80,6 @@ static std::vector<int2> make_tiles(const std::vector<int32_t> &rs, int64_t nrow
   return out;
 }
 
-// The pipelined gather's tiles (bs_gather.cuh): consecutive rows while the
-// tile holds at most kAgEntries CSR entries, kAgRows rows and kAgChunks
-// distinct 16-byte chunks of q_L; per tile the sorted chunk ids, then a blob
-// of uint16 entry offsets (slot * 2 + the value's half of its chunk) and
-// uint16 row starts relative to the tile's first entry, then the tile's rows
-// (uint16, relative to its first row) in the order the kernel sums them, each
-// part padded to 8 values.  A row that alone exceeds a tile gets a tile of its
-// own marked -1.  With N_L odd the 16-byte chunk of the last local node would
-// run past q_L, so the row holding that node (one row at most) gets a tile of
-// its own marked -1 as well and no chunk covers it.
-struct AgTiles {
-  std::vector<int4> info;
-  std::vector<int32_t> chunks;
-  std::vector<uint16_t> blob;
-};
-
-static AgTiles build_async_tiles(const std::vector<int32_t> &rs, const std::vector<int32_t> &col,
-                                 int64_t NL, int64_t NG) {
-  AgTiles T;
-  std::vector<int32_t> mark((size_t)((NL + 1) / 2), -1);
-  std::vector<int32_t> ch;
-  int32_t tile = 0;
-  // N_L odd: the row holding local node N_L - 1, summed straight from the CSR
-  int64_t direct_row = -1;
-  if (NL % 2 == 1)
-    for (int64_t g = 0; g < NG && direct_row < 0; ++g)
-      if (rs[(size_t)g] < rs[(size_t)g + 1] && col[(size_t)rs[(size_t)g + 1] - 1] == NL - 1)
-        direct_row = g;
-  auto row_chunks_new = [&](int64_t r) {  // chunks of row r not yet in the tile
-    int fresh = 0;
-    for (int32_t k = rs[(size_t)r]; k < rs[(size_t)r + 1]; ++k) {
-      const int32_t c = col[(size_t)k] >> 1;
-      if (mark[(size_t)c] == tile) continue;
-      bool dup = false;
-      for (int32_t q = rs[(size_t)r]; q < k && !dup; ++q) dup = (col[(size_t)q] >> 1) == c;
-      fresh += !dup;
-    }
-    return fresh;
-  };
-  for (int64_t g = 0; g < NG;) {
-    int64_t r = g;
-    ch.clear();
-    while (r < NG && r != direct_row && r - g < kAgRows &&
-           rs[(size_t)r + 1] - rs[(size_t)g] <= kAgEntries &&
-           (int)ch.size() + row_chunks_new(r) <= kAgChunks) {
-      for (int32_t k = rs[(size_t)r]; k < rs[(size_t)r + 1]; ++k) {
-        const int32_t c = col[(size_t)k] >> 1;
-        if (mark[(size_t)c] != tile) {
-          mark[(size_t)c] = tile;
-          ch.push_back(c);
-        }
-      }
-      ++r;
-    }
-    int4 in;
-    in.x = (int)g;
-    in.y = (int)T.chunks.size();
-    in.z = (int)(T.blob.size() / 8);
-    if (r == g) {  // one row too long for a tile, or the row of the odd last node
-      in.w = -1;
-      r = g + 1;
-    } else {
-      std::sort(ch.begin(), ch.end());
-      const int32_t k0 = rs[(size_t)g], nk = rs[(size_t)r] - k0;
-      in.w = (nk << 16) | (int)(r - g);
-      T.chunks.insert(T.chunks.end(), ch.begin(), ch.end());
-      for (int32_t k = k0; k < k0 + nk; ++k) {
-        const int32_t c = col[(size_t)k] >> 1;
-        const int32_t slot = (int32_t)(std::lower_bound(ch.begin(), ch.end(), c) - ch.begin());
-        T.blob.push_back((uint16_t)(slot * 2 + (col[(size_t)k] & 1)));
-      }
-      while (T.blob.size() % 8) T.blob.push_back(0);
-      for (int64_t q = g; q <= r; ++q) T.blob.push_back((uint16_t)(rs[(size_t)q] - k0));
-      while (T.blob.size() % 8) T.blob.push_back(0);
-      // the summing order: rows by length, longest first (stable)
-      std::vector<int32_t> ord((size_t)(r - g));
-      for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int32_t)q;
-      auto len = [&](int32_t q) { return rs[(size_t)g + q + 1] - rs[(size_t)g + q]; };
-      std::stable_sort(ord.begin(), ord.end(),
-                       [&](int32_t a, int32_t b) { return len(a) > len(b); });
-      for (int32_t q : ord) T.blob.push_back((uint16_t)q);
-      while (T.blob.size() % 8) T.blob.push_back(0);
-    }
-    T.info.push_back(in);
-    ++tile;
-    g = r;
-  }
-  int4 last;
-  last.x = (int)NG;
-  last.y = (int)T.chunks.size();
-  last.z = (int)(T.blob.size() / 8);
-  last.w = 0;
-  T.info.push_back(last);
-  return T;
-}
-
 template <typename V>
 static cudaError_t upload(V **d, const std::vector<V> &h, size_t pad = 0) {
   cudaError_t e = cudaMalloc(d, sizeof(V) * (h.size() + pad + (h.empty() && !pad ? 1 : 0)));
@@ -286,7 +190,10 @@ int bs_map_create(int32_t E, int32_t N, int64_t NG, const int32_t *h_l2g, bs_map
   if (e == cudaSuccess && NG > 0) {  // the pipelined FP64 gather's tiles
     AgTiles T = build_async_tiles(rs, col, NL, NG);
     m->ag_ntiles = (int64_t)T.info.size() - 1;
-    e = upload(&m->d_ag_info, T.info);
+    static_assert(sizeof(AgInfo) == sizeof(int4), "tile info is the kernel's int4");
+    std::vector<int4> info(T.info.size());
+    memcpy(info.data(), T.info.data(), sizeof(int4) * info.size());
+    e = upload(&m->d_ag_info, info);
     if (e == cudaSuccess) e = upload(&m->d_ag_chunks, T.chunks, 4);
     std::vector<uint4> words(T.blob.size() / 8);
     if (!words.empty()) memcpy(words.data(), T.blob.data(), T.blob.size() * sizeof(uint16_t));
