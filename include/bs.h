@@ -133,8 +133,8 @@ int bs_cg_update_f32(int64_t n, float alpha, const float *p, const float *Ap,
  * local node l (Sec. 5: boundary conditions).  Every h_l2g[l] must be < NG.
  * bs_map_create copies the map to the device and builds the CSR form of Z^T
  * (Sec. 5, Listing 4): rowStarts[NG+1] and colIds[nnz], the local indices of
- * each global node in ascending order, and the FP64 gather's per-tile
- * re-encoding of it (the distinct 16-byte chunks of q_L each tile reads, uint16
+ * each global node in ascending order, and the gather's per-tile re-encoding
+ * of it (the distinct chunks of two q_L values each tile reads, uint16
  * offsets, row starts and summing order: about 4 more bytes of device memory
  * per local node and 4 per global node).  Host-side, synchronous. */
 typedef struct bs_map bs_map;
