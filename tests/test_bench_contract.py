@@ -42,3 +42,21 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["config"]["workload"] and d["config"]["n"] == 1 << 18
     assert "n=2^18" in d["cpu_baseline"]["sample"]
+
+
+def test_roofline_kernel_names_are_the_kernels_the_ops_launch():
+    """Each op's kernel named in the bench line (roofline.kernel) is a
+    __global__ kernel of the library, and the one-op-per-kernel mapping
+    matches the launcher each op calls (BS3: the split norm, BS6: the
+    pipelined gather)."""
+    import re
+    src = ""
+    csrc = os.path.join(ROOT, "paper_2009_10917_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            src += open(os.path.join(csrc, f)).read()
+    kernels = set(re.findall(r"__global__\s+void\s+(?:__launch_bounds__\([^)]*\)\s+)?(\w+)", src))
+    assert set(bench.KERNEL_OF) == set(bench.OPS)
+    for op, k in bench.KERNEL_OF.items():
+        assert k in kernels, (op, k)
+    assert bench.KERNEL_OF["norm"] == "k_norm_split" and bench.KERNEL_OF["gather"] == "k_gather_async"
